@@ -1,0 +1,178 @@
+"""Seeded synthetic workloads of the thermionic He diode.
+
+This module only *describes inputs*: parameter sets (plain dicts of SI
+numbers) and seeded particle states drawn with numpy.  It holds none of the
+method's arithmetic, imports neither the CUDA library nor the oracle, and is
+the one module both of them are fed from.
+
+Parameter dict keys (SI units unless the key says otherwise):
+  L, V, Nz, dt, gamma_emit, T_wall_K, n_gas, T_gas_e_K, T_gas_i_K, T_e0_eV,
+  T_i0_eV, weight, m_ion, m_gas, sigma_el_e, sigma_cx_i, sigma_el_i,
+  E_exc_eV, sigma_exc0, E_iz_eV, lotz_a, lotz_q, E_cap_e_eV, E_cap_i_eV,
+  replenish, window_start, seed
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+E_CHARGE = 1.602176634e-19
+M_E = 9.1093837015e-31
+K_B = 1.380649e-23
+M_HE = 4.002602 * 1.66053906660e-27          # He atom
+M_HE_ION = M_HE - M_E                        # He+
+
+
+def he_defaults() -> dict:
+    """Cross-section and species constants shared by all He workloads.
+
+    Elastic 6e-20 m^2 and CX 3e-19 m^2 are the analytic-fit values of the
+    single-diode workload; excitation threshold 19.8 eV with a linear-onset
+    fit sigma0 (1 - E_th/E), sigma0 = 5e-22 m^2; ionisation threshold 24.6 eV
+    with a Lotz form a q ln(E/P)/(E P), a = 4e-18 m^2 eV^2, q = 2.
+    """
+    return dict(
+        m_ion=M_HE_ION, m_gas=M_HE,
+        sigma_el_e=6e-20, sigma_cx_i=3e-19, sigma_el_i=0.0,
+        E_exc_eV=19.8, sigma_exc0=5e-22,
+        E_iz_eV=24.6, lotz_a=4.0e-18, lotz_q=2.0,
+        E_cap_e_eV=60.0, E_cap_i_eV=60.0,
+        T_gas_e_K=300.0, T_gas_i_K=300.0,
+        T_e0_eV=3.0, T_i0_eV=0.15,
+        replenish=0, window_start=0,
+    )
+
+
+def vacuum_transit_time(gap_m: float, bias_V: float) -> float:
+    """Uniform-field transit time from rest, sqrt(2 d^2 m_e / (e V))."""
+    return math.sqrt(2.0 * gap_m * gap_m * M_E / (E_CHARGE * bias_V))
+
+
+def weight_for_in_flight(gamma: float, gap_m: float, bias_V: float, n_flight: float) -> float:
+    """Macro weight giving ~n_flight emitted electrons in a vacuum-transit gap."""
+    return gamma * vacuum_transit_time(gap_m, bias_V) / n_flight
+
+
+def single_diode_small(seed: int = 1) -> dict:
+    """1 mm He diode, 128 cells, dt 1e-12 s, 2000 steps, starts empty, +10 V.
+
+    n_He 2e21 m^-3 at 300 K, T_w = 2500 K, Gamma = 7.25e19 m^-2 s^-1, weight
+    chosen for ~2e4 emitted electrons in flight.
+    """
+    p = he_defaults()
+    p.update(L=1e-3, V=10.0, Nz=128, dt=1e-12, n_gas=2e21, T_wall_K=2500.0,
+             gamma_emit=7.25e19, seed=seed, n_steps=2000, window_start=1000)
+    p["weight"] = weight_for_in_flight(p["gamma_emit"], p["L"], p["V"], 2.0e4)
+    return p
+
+
+def single_diode_production(seed: int = 2) -> dict:
+    """5 mm He diode, 2048 cells, dt 5e-13 s, 20000 steps, ~8M e + ~2M He+.
+
+    Same physics as the small diode; weight sized for ~8e6 emitted electrons in
+    flight (about 750 emitted per step).
+    """
+    p = he_defaults()
+    p.update(L=5e-3, V=10.0, Nz=2048, dt=5e-13, n_gas=2e21, T_wall_K=2500.0,
+             gamma_emit=7.25e19, seed=seed, n_steps=20000, window_start=10000)
+    p["weight"] = weight_for_in_flight(p["gamma_emit"], p["L"], p["V"], 8.0e6)
+    return p
+
+
+def paper_diode(gamma_emit: float = 7.25e19, seed: int = 3) -> dict:
+    """The paper's benchmark diode (Sec. 2.1-2.2): 10 cm, 4096 cells, 40 V."""
+    p = he_defaults()
+    L, Nz, n0, ppc = 0.10, 4096, 5e14, 1000
+    Te0 = 3.0
+    vte = math.sqrt(E_CHARGE * Te0 / M_E)
+    dz = L / Nz
+    p.update(L=L, V=40.0, Nz=Nz, dt=0.2 * dz / vte, n_gas=2.9e21,
+             sigma_el_e=6.8877e-20, sigma_cx_i=1.7241e-20, sigma_exc0=0.0, lotz_a=0.0,
+             T_gas_e_K=300.0, T_gas_i_K=1740.0, T_e0_eV=Te0, T_i0_eV=0.15,
+             T_wall_K=0.2 * E_CHARGE / K_B, gamma_emit=gamma_emit, replenish=1,
+             weight=n0 * dz / ppc, seed=seed, n_steps=4_500_000)
+    p["n0"] = n0
+    p["ppc"] = ppc
+    return p
+
+
+def maxwellian(rng: np.random.Generator, n: int, T_eV: float, mass: float):
+    s = math.sqrt(E_CHARGE * T_eV / mass)
+    return (rng.standard_normal(n) * s, rng.standard_normal(n) * s, rng.standard_normal(n) * s)
+
+
+def uniform_plasma(rng: np.random.Generator, n: int, L: float, T_e_eV: float, T_i_eV: float,
+                   m_ion: float = M_HE_ION):
+    """n electrons and n ions uniform on [0, L) with Maxwellian velocities."""
+    ze = (rng.random(n) * L).astype(np.float32)
+    zi = (rng.random(n) * L).astype(np.float32)
+    ve = [v.astype(np.float32) for v in maxwellian(rng, n, T_e_eV, M_E)]
+    vi = [v.astype(np.float32) for v in maxwellian(rng, n, T_i_eV, m_ion)]
+    return (ze, *ve), (zi, *vi)
+
+
+def emitted_fill(rng: np.random.Generator, n: int, L: float, T_wall_K: float):
+    """n emitted-type electrons uniform on [0, L), flux-weighted T_w velocities."""
+    s = math.sqrt(K_B * T_wall_K / M_E)
+    z = (rng.random(n) * L).astype(np.float32)
+    vx = (rng.standard_normal(n) * s).astype(np.float32)
+    vy = (rng.standard_normal(n) * s).astype(np.float32)
+    vz = (rng.rayleigh(s, n)).astype(np.float32)
+    return z, vx, vy, vz
+
+
+def clamp_inside(z: np.ndarray, L: float) -> np.ndarray:
+    """Keep FP32 positions strictly inside [0, L)."""
+    Lf = np.float32(L)
+    z = np.asarray(z, np.float32)
+    return np.where(z >= Lf, np.nextafter(Lf, np.float32(0)), np.maximum(z, np.float32(0)))
+
+
+def production_preload(p: dict, seed: int = 20, n_emit: int = 6_000_000,
+                       n_pairs: int = 2_000_000):
+    """Synthetic loaded state for the 5 mm diode: 6M emitted-type electrons
+    (uniform position, T_w velocities) + 2M plasma e-He+ pairs (Te0 3 eV,
+    Ti0 0.15 eV).  Returns {species: (z, vx, vy, vz)}."""
+    rng = np.random.default_rng(seed)
+    em = emitted_fill(rng, n_emit, p["L"], p["T_wall_K"])
+    pe, pi = uniform_plasma(rng, n_pairs, p["L"], p["T_e0_eV"], p["T_i0_eV"], p["m_ion"])
+    out = {0: em, 1: pe, 2: pi}
+    for k in out:
+        z, vx, vy, vz = out[k]
+        out[k] = (clamp_inside(z, p["L"]), vx, vy, vz)
+    return out
+
+
+def scaled_preload(p: dict, seed: int, n_emit: int, n_pairs: int):
+    """Same recipe as production_preload at an arbitrary size."""
+    return production_preload(p, seed=seed, n_emit=n_emit, n_pairs=n_pairs)
+
+
+def batched_sweep(n_instances: int = 64, seed: int = 1000, n_steps: int = 10000):
+    """Independent He diodes of uneven size for the batched flux sweep.
+
+    Gamma ~ U[5e19, 9e19], gap ~ U[1, 5] mm with cells = gap / 2.5 um,
+    n_He ~ logU[1e21, 1e22], target emitted-electron count ~ logU[5e4, 4e6]
+    reached through the weight, V = 10 V, dt bounded so a 60 eV electron
+    crosses at most half a cell per step.  Instance i uses seed + i.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_instances):
+        p = he_defaults()
+        gap = float(rng.uniform(1e-3, 5e-3))
+        Nz = int(round(gap / 2.5e-6))
+        gamma = float(rng.uniform(5e19, 9e19))
+        n_gas = float(10 ** rng.uniform(21, 22))
+        target = float(10 ** rng.uniform(math.log10(5e4), math.log10(4e6)))
+        dz = gap / Nz
+        v_cap = math.sqrt(2 * 60.0 * E_CHARGE / M_E)
+        dt = min(1e-12, 0.5 * dz / v_cap)
+        p.update(L=gap, V=10.0, Nz=Nz, dt=dt, n_gas=n_gas, T_wall_K=2500.0,
+                 gamma_emit=gamma, seed=seed + i, n_steps=n_steps,
+                 window_start=n_steps // 2)
+        p["weight"] = weight_for_in_flight(gamma, gap, 10.0, target)
+        p["target_in_flight"] = target
+        out.append(p)
+    return out
