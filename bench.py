@@ -1,0 +1,327 @@
+"""Throughput of the PIC-MCC diode step on GB300.
+
+Workload: the production-size single He diode (5 mm gap, 2048 cells, dt 5e-13
+s, 10 V; elastic + excitation + Lotz ionisation for e-He, CX for He+-He),
+preloaded with a synthetic state of 6M emitted-type electrons and 2M plasma
+e-He+ pairs (~10M macro-particles, 200 MB of streamed state: larger than L2).
+One bench step = one PIC time step of the whole hot path: deposit/field,
+gather+push+absorb, MCC, compaction, emission, replenishment.
+
+Metric: particle-steps/s (sum over steps of live particles pushed / time).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun: every rank advances its own independent replica
+diode (different seed), no data-path collective; value is the sum over ranks.
+The reference arm times the CPU oracle on a bounded sample of the same state.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2605_07083_gb300 import workloads as W  # noqa: E402
+
+ALG_BYTES_PER_PARTICLE = 20      # read z, v_z, id + write z, v_z (FP32/u32)
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def workload(seed_offset=0):
+    p = W.single_diode_production(seed=2 + seed_offset)
+    p["capacity"] = (8_000_000, 3_000_000, 3_000_000)
+    return p
+
+
+def describe(p, n0):
+    return {"workload": "single He diode 5 mm, 2048 cells, dt 5e-13 s, 10 V, preloaded "
+                        "6M emitted e + 2M plasma e-He+ pairs",
+            "cells": p["Nz"], "particles_initial": int(n0), "dt_s": p["dt"],
+            "weight_m2": p["weight"], "l2": "inputs larger than L2 (~200 MB streamed per step)",
+            "pic_steps_per_bench_step": 1}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+                for n, v in zip(names, r[4:8]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                pass
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world):
+    import torch
+    from paper_2605_07083_gb300 import build as B
+    B.build()
+    from paper_2605_07083_gb300 import pic
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    p = workload(seed_offset=rank)
+    state = W.production_preload(p, seed=20 + rank)
+    n0 = sum(state[s][0].size for s in range(3))
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+
+    def barrier():
+        if dist:
+            td.barrier()
+        torch.cuda.synchronize()
+
+    d = pic.Diode(p)
+    for sp in range(3):
+        d.inject(sp, *state[sp])
+    d.step(args.warmup)
+    d.synchronize()
+    stream = d.stream
+    # --- timed region 1: graph-launched steps (value)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.3)
+    pushed0 = d.diagnostics()["particles_pushed"]
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    d.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    pushed = d.diagnostics()["particles_pushed"] - pushed0
+    # --- timed region 2: same steps with CUDA events around every kernel
+    pushed1 = d.diagnostics()["particles_pushed"]
+    prof = d.profile(args.steps)
+    pushed_prof = d.diagnostics()["particles_pushed"] - pushed1
+    ck = clocks.stop()
+    diag = d.diagnostics()
+    d.close()
+    del d
+    torch.cuda.synchronize()
+
+    # --- end to end through the C ABI: host (pinned) state in, K steps, diag out
+    pinned = {}
+    h2d = 0
+    for sp in range(3):
+        pinned[sp] = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in state[sp]]
+        h2d += sum(t.numel() * 4 for t in pinned[sp])
+    lib = pic.load()
+    import ctypes as C
+    h = pic.pic_create([pic.make_config(p)], C.c_void_p(stream.cuda_stream),
+                       None)
+    barrier()
+    t0 = time.perf_counter()
+    for sp in range(3):
+        n = pinned[sp][0].numel()
+        rc = lib.pic_inject(h, 0, sp, n, *[C.c_void_p(t.data_ptr()) for t in pinned[sp]], 0)
+        assert rc == 0, rc
+    lib.pic_step(h, args.warmup + args.steps)
+    dg = pic.PicDiag()
+    rc = lib.pic_diagnostics(h, 0, C.byref(dg))
+    t1 = time.perf_counter()
+    barrier()
+    e2e_ps = dg.particles_pushed
+    lib.pic_destroy(h)
+    e2e_s = t1 - t0
+    n_e2e_steps = args.warmup + args.steps
+
+    # --- reduce over ranks
+    vals = torch.tensor([ms, float(pushed), e2e_s, float(e2e_ps)], dtype=torch.float64, device="cuda")
+    if dist:
+        mx = vals.clone()
+        td.all_reduce(mx, op=td.ReduceOp.MAX)
+        sm = vals.clone()
+        td.all_reduce(sm, op=td.ReduceOp.SUM)
+        ms_max, pushed_tot, e2e_max, e2e_tot = mx[0].item(), sm[1].item(), mx[2].item(), sm[3].item()
+    else:
+        ms_max, pushed_tot, e2e_max, e2e_tot = ms, float(pushed), e2e_s, float(e2e_ps)
+    if rank != 0:
+        return None
+    value = pushed_tot / (ms_max * 1e-3)
+    peak, peak_kind = hbm_peak()
+    push_ms = prof["ms_push"] / max(prof["push_launches"], 1)
+    n_per_launch = pushed_prof / max(prof["push_launches"], 1)
+    achieved = ALG_BYTES_PER_PARTICLE * n_per_launch / (push_ms * 1e-3) / 1e9
+    cpu = cpu_baseline(p, state) if not args.no_cpu else None
+    launches = 3 * args.steps
+    out = {
+        "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": describe(p, n0),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_push", "peak_kind": peak_kind + " (hbm_gbs)",
+                     "alg_bytes_per_particle": ALG_BYTES_PER_PARTICLE,
+                     "particles_per_launch": n_per_launch, "avg_launch_ms": push_ms,
+                     "ms_mcc_per_step": prof["ms_mcc"] / max(args.steps, 1),
+                     "ms_post_per_step": prof["ms_post"] / max(args.steps, 1),
+                     "ms_step_profiled": prof["ms_total"] / max(args.steps, 1)},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_tot / e2e_max, "unit": "particle-steps/s",
+                "h2d_bytes_per_step": h2d / n_e2e_steps,
+                "d2h_bytes_per_step": C.sizeof(pic.PicDiag) / n_e2e_steps,
+                "steps": n_e2e_steps, "includes": "pic_inject from pinned host + pic_step + "
+                                                   "pic_diagnostics"},
+        "gpu_launches": launches,
+        "clocks": ck,
+        "diag": {"n_live": diag["n_live"], "backflow_ratio": diag["backflow_ratio"],
+                 "candidates": diag["candidates"].tolist()},
+    }
+    return out
+
+
+def cpu_baseline(p, state, budget_s=12.0):
+    """The oracle as it stands, on the host, single thread: a bounded number of
+    steps of the same preloaded production state."""
+    from oracle import oracle as O
+    o = O.Oracle(p)
+    for sp in range(3):
+        o.inject(sp, *state[sp])
+    n = sum(o.count(s) for s in range(3))
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        o.step(1)
+        steps += 1
+        if time.perf_counter() - t0 > budget_s or steps >= 50:
+            break
+    el = time.perf_counter() - t0
+    return {"value": n * steps / el, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": "full %d-particle production state, %d steps, single-threaded FP64 C++"
+                      % (n, steps)}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from oracle import oracle as O
+    O.build()
+    p = workload()
+    full = W.production_preload(p, seed=20)
+    n_full = sum(full[s][0].size for s in range(3))
+    # each step: the oracle advances a fixed random subsample of the state
+    total_budget = 90.0
+    per_step_particles = 2.0e7 * total_budget / max(args.steps + args.warmup, 1)
+    frac = min(1.0, per_step_particles / n_full)
+    rng = np.random.default_rng(5)
+    sample = {}
+    for sp in range(3):
+        n = full[sp][0].size
+        idx = np.sort(rng.choice(n, max(1, int(n * frac)), replace=False))
+        sample[sp] = tuple(a[idx] for a in full[sp])
+    o = O.Oracle(p)
+    for sp in range(3):
+        o.inject(sp, *sample[sp])
+    for _ in range(args.warmup):
+        o.step(1)
+    done = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        done += sum(o.count(s) for s in range(3))
+        o.step(1)
+    el = time.perf_counter() - t0
+    v = done / el
+    return {"impl": "reference", "metric": "particle-steps/s", "value": v,
+            "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": describe(p, n_full),
+            "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": 1,
+                             "kind": "oracle",
+                             "sample": "%.4f of the production state per step (%d particles)"
+                                       % (frac, sum(sample[s][0].size for s in range(3)))},
+            "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        td.init_process_group("nccl")
+    out = run_reference(args, rank, world) if args.impl == "reference" else run_ours(args, rank, world)
+    if out is not None:
+        print(json.dumps(out))
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as td
+        td.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,227 @@
+/*
+ * pic.h -- C ABI of the GB300 PIC-MCC thermionic-diode library.
+ *
+ * The library advances 1D-in-space, 3D-in-velocity electrostatic
+ * particle-in-cell / Monte Carlo collision models of planar He diodes with a
+ * thermionically emitting cathode (arXiv 2605.07083, Sec. 2.1-2.4), one or
+ * many independent diodes ("instances") per handle, on one CUDA device.
+ *
+ * Conventions for every entry point
+ *   - Plain pointers and sizes only.  Pointers named "host" or used with
+ *     on_device == 0 are host memory; with on_device != 0 they are device
+ *     memory of the handle's device.  The caller owns every buffer it passes;
+ *     the library reads or writes it only during the call (device buffers:
+ *     until the call's work on the handle's stream has finished).
+ *   - The library owns all simulation state (particles, grids, tallies).
+ *   - Every function returns PIC_OK (0) or a negative PIC_E* code; nothing
+ *     aborts or exits.  Work is enqueued on the handle's CUDA stream.
+ *     Device-side failures (capacity overflow, null-collision bound exceeded)
+ *     raise sticky flags that the next synchronising call returns.
+ *   - Species: 0 = emitted (thermionic) electrons, 1 = plasma electrons,
+ *     2 = He+ ions (Sec. 2.2 tracks emitted and plasma electrons separately).
+ *     Walls: 0 = cathode at z = 0, 1 = anode at z = L.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_ABI_VERSION 1
+
+enum {
+    PIC_OK = 0,
+    PIC_EINVAL = -1,      /* bad argument or configuration */
+    PIC_ENOMEM = -2,      /* device allocation failed */
+    PIC_ECUDA = -3,       /* a CUDA runtime call failed */
+    PIC_ECAPACITY = -4,   /* a species outgrew its capacity; extra particles dropped */
+    PIC_ETIMEOUT = -5,    /* a bounded device wait gave up */
+    PIC_EENERGYCAP = -6   /* a collision candidate exceeded the null-collision bound */
+};
+
+enum { PIC_SPECIES_EMITTED = 0, PIC_SPECIES_PLASMA_E = 1, PIC_SPECIES_ION = 2 };
+
+/*
+ * One diode.  Copied at pic_create.  Paper references:
+ *   gap_m, bias_V, n_cells, dt_s: Sec. 2.1 (Dirichlet phi(0)=0, phi(L)=bias_V)
+ *   gamma_emit, T_wall_K: Sec. 2.2 (imposed flux, emission temperature T_c)
+ *   n_gas, sigma_el_e, sigma_cx_i, T_gas_e_K, T_gas_i_K: Sec. 2.2 (MCC)
+ *   weight: Sec. 2.1 (planar macro-particle weight w0, m^-2; one value for
+ *           all species of the instance)
+ *   replenish, T_e0_eV, T_i0_eV: Sec. 2.1 (ion-loss replenishment)
+ *   E_exc_eV, sigma_exc0: excitation channel, fit sigma0 (1 - E_th/E)
+ *           (the paper's dataset is not published; sigma_exc0 = 0 disables)
+ *   E_iz_eV, lotz_a, lotz_q: Lotz ionisation a q ln(E/P)/(E P) (not in the
+ *           paper; lotz_a = 0 disables)
+ *   E_cap_e_eV, E_cap_i_eV: bound on the relative collision energy used for
+ *           the null-collision frequency nu_max (exceeding it raises
+ *           PIC_EENERGYCAP)
+ *   window_start: first step whose boundary fluxes enter the late-time
+ *           averages of pic_diagnostics (Sec. 2.3)
+ *   capacity: particle capacity per species (0 = choose automatically)
+ */
+typedef struct pic_config {
+    uint32_t size;            /* sizeof(pic_config): ABI check */
+    int32_t n_cells;          /* Nz, 1 <= Nz <= 4096 */
+    double gap_m;             /* L, m */
+    double bias_V;            /* phi(L), V */
+    double dt_s;              /* time step, s */
+    double gamma_emit;        /* m^-2 s^-1 */
+    double T_wall_K;          /* emission temperature, K */
+    double n_gas;             /* m^-3 */
+    double T_gas_e_K;         /* neutral partner temperature for e-He, K */
+    double T_gas_i_K;         /* neutral partner temperature for He+-He, K */
+    double T_e0_eV;           /* replenished electron temperature, eV */
+    double T_i0_eV;           /* replenished ion temperature, eV */
+    double weight;            /* m^-2 */
+    double m_ion;             /* kg */
+    double m_gas;             /* kg */
+    double sigma_el_e;        /* m^2 */
+    double sigma_cx_i;        /* m^2 */
+    double sigma_el_i;        /* m^2 */
+    double E_exc_eV;
+    double sigma_exc0;        /* m^2 */
+    double E_iz_eV;
+    double lotz_a;            /* m^2 eV^2 */
+    double lotz_q;
+    double E_cap_e_eV;
+    double E_cap_i_eV;
+    int32_t replenish;        /* 0 / 1 */
+    int32_t reserved0;
+    int64_t window_start;
+    uint64_t seed;            /* Philox key material */
+    int64_t capacity[3];
+} pic_config;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  NULL in
+ * pic_create means cudaMallocAsync / cudaFreeAsync on the handle's stream. */
+typedef struct pic_allocator {
+    void* (*alloc)(size_t bytes, void* cuda_stream, void* ctx);
+    void (*free)(void* ptr, size_t bytes, void* cuda_stream, void* ctx);
+    void* ctx;
+} pic_allocator;
+
+/* Launch shape and scheduling knobs (pic_tune).  Zero keeps the current value. */
+typedef struct pic_tuning {
+    uint32_t size;            /* sizeof(pic_tuning) */
+    int32_t push_threads;     /* threads per block of the particle kernels (64..1024, multiple of 32) */
+    int32_t push_blocks_per_sm;
+    int32_t sort_period;      /* counting sort by cell every this many steps; < 0 disables */
+    int32_t graph_steps;      /* steps captured per CUDA graph; < 0 disables graphs */
+    int32_t reserved[3];
+} pic_tuning;
+
+/* Late-time diagnostics of one instance (Sec. 2.3, Eq. 1-8).  Fluxes in
+ * m^-2 s^-1, energies in J m^-2, powers in W m^-2, temperatures in eV. */
+typedef struct pic_diag {
+    int64_t step;                 /* index of the next step to run */
+    int64_t window_steps;         /* steps accumulated in the window */
+    double window_time;           /* window_steps * dt */
+    int64_t n_live[3];
+    int64_t count[3][2];          /* absorbed macro-particles per species, wall */
+    double ke[3][2];              /* absorbed kinetic energy * weight */
+    int64_t emitted;              /* thermionic macro-electrons emitted */
+    int64_t replenished;          /* e-ion pairs re-injected */
+    int64_t collisions[6];        /* null, e-He elastic, excitation, ionisation, CX, He+-He elastic */
+    int64_t candidates[3];        /* null-collision candidates per species */
+    int64_t energy_cap_exceeded;
+    int64_t particles_pushed;     /* particle-steps done since creation (all windows) */
+    double gamma_emit, gamma_emit_realized, gamma_ref, gamma_net, gamma_anode;
+    double backflow_ratio;        /* Gamma_ref / Gamma_emit */
+    double net_efficiency;        /* Gamma_net / Gamma_emit */
+    double collection_efficiency; /* Gamma_anode / Gamma_emit */
+    double T_c_eV, W_F_eff, q_emit_theory;                               /* Eq. 1-2 */
+    double q_back_em_cath, q_back_p_cath, q_ion_cath, gamma_ion_cath;
+    double q_ion_cath_recomb;                                            /* Eq. 3 */
+    double q_cooling_1, q_cooling_2;                                     /* Eq. 4-5 */
+    double q_out_em_anode, q_out_p_anode, q_ion_anode, gamma_ion_anode;
+    double q_anode_total_1, q_ion_anode_recomb, q_anode_total_2;         /* Eq. 6-8 */
+    int32_t error_flags;          /* bit (-code - 1) set for each sticky PIC_E* code */
+    int32_t reserved;
+} pic_diag;
+
+/* Per-kernel device time of pic_profile_steps, milliseconds (CUDA events). */
+typedef struct pic_profile {
+    int64_t steps;
+    double ms_push;               /* gather+push+absorb+candidate test+deposit kernel */
+    double ms_mcc;                /* collisions of the step's candidates */
+    double ms_post;               /* compaction+injection+field solve kernel */
+    double ms_sort;               /* counting sort kernels */
+    double ms_total;
+    int64_t particle_steps;       /* live particles pushed, summed over steps */
+    int64_t launches;             /* kernels launched */
+    int64_t push_launches;
+} pic_profile;
+
+typedef struct pic_handle pic_handle;
+
+/* Create n_instances independent diodes on the current CUDA device.
+ * cfgs: n_instances configs (host).  cuda_stream: cudaStream_t or NULL for
+ * the legacy default stream.  alloc: optional device allocator.  The handle
+ * starts empty at step 0.  Sec. 2.1 (grid, Poisson), 2.2 (MCC constants). */
+int pic_create(const pic_config* cfgs, int n_instances, void* cuda_stream,
+               const pic_allocator* alloc, pic_handle** out);
+
+/* Append n particles of one species to an instance (Sec. 2.1 initial
+ * loading).  z in [0, gap_m); velocities in m s^-1, FP32.  Particles get the
+ * instance's next ids in order.  Returns PIC_ECAPACITY (nothing appended) if
+ * they do not fit, PIC_EINVAL if a host z lies outside [0, L).  Synchronises
+ * the stream. */
+int pic_inject(pic_handle* h, int instance, int species, int64_t n, const float* z,
+               const float* vx, const float* vy, const float* vz, int on_device);
+
+/* Advance every instance by n_steps time steps (Sec. 2.1-2.2 step: deposit,
+ * Poisson, gather, push, absorb, MCC, emit, replenish, compact).
+ * Asynchronous; returns a sticky error seen earlier, else PIC_OK. */
+int pic_step(pic_handle* h, int64_t n_steps);
+
+/* Same steps as pic_step, launched one by one with CUDA events around each
+ * kernel; synchronises and reports per-kernel device time. */
+int pic_profile_steps(pic_handle* h, int64_t n_steps, pic_profile* out);
+
+/* Window tallies and Eq. 1-8 diagnostics of one instance.  Synchronises. */
+int pic_diagnostics(pic_handle* h, int instance, pic_diag* out);
+
+/* Copy out the live particles of one species.  cap = room in the buffers;
+ * *n receives the live count (PIC_ECAPACITY if cap < *n, nothing copied).
+ * Any buffer may be NULL.  Synchronises. */
+int pic_get_state(pic_handle* h, int instance, int species, float* z, float* vx, float* vy,
+                  float* vz, uint32_t* id, int64_t cap, int64_t* n, int on_device);
+
+/* Fixed-point charge rho of the current state on the n_cells+1 nodes, in
+ * units of e*weight/2^24 (signed).  Synchronises. */
+int pic_get_rho_fixed(pic_handle* h, int instance, int64_t* out, int64_t n_nodes);
+
+/* phi (V, FP64) and E (V/m, the FP32 copy the push gathers) on the nodes
+ * for the current state; either pointer may be NULL.  Synchronises. */
+int pic_get_field(pic_handle* h, int instance, double* phi, float* E, int64_t n_nodes);
+
+/* Set the step index of every instance (Philox counters use it). */
+int pic_set_step(pic_handle* h, int64_t step);
+
+/* Change launch knobs (see pic_tuning). */
+int pic_tune(pic_handle* h, const pic_tuning* t);
+
+/* Sort every species of every instance by cell now (stable counting sort). */
+int pic_sort(pic_handle* h);
+
+/* Wait for the stream; return the first sticky error. */
+int pic_synchronize(pic_handle* h);
+
+/* Release the handle and all device state it owns.  NULL is ignored. */
+void pic_destroy(pic_handle* h);
+/* Static description of a PIC_E* code. */
+const char* pic_strerror(int code);
+int pic_abi_version(void);
+/* sizeof of the ABI structs for foreign bindings: 0 pic_config, 1 pic_tuning,
+ * 2 pic_diag, 3 pic_profile; 0 for anything else. */
+size_t pic_sizeof(int which);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIC_H */

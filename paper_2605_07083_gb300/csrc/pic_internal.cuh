@@ -1,0 +1,219 @@
+// pic_internal.cuh -- device-side state layout and helpers of the PIC-MCC
+// library.  Internal to the library; the public boundary is include/pic.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pic {
+
+constexpr int kMaxNz = 4096;          // shared-memory grid limit (nodes = Nz + 1)
+constexpr int kMaxInstances = 256;
+constexpr int kEvCap = 2048;          // ionisation events per instance per step
+constexpr int kPostThreads = 1024;
+constexpr int kTwo24 = 1 << 24;
+
+enum Tag : uint32_t { TAG_MCC = 1, TAG_EMIT = 2, TAG_EMIT_N = 3, TAG_REPL = 4 };
+constexpr uint32_t kStreamInject = 3;
+
+// sticky error bits: bit (-code - 1)
+enum ErrBit : int32_t { ERR_CAPACITY = 1 << 3, ERR_TIMEOUT = 1 << 4, ERR_ENERGYCAP = 1 << 5 };
+
+constexpr int kMccThreads = 256;
+
+// Per-instance constants, derived on the host in FP64 and stored once.
+struct InstConst {
+  int32_t Nz;
+  int32_t node_off;        // first node of this instance in the node arrays
+  float inv_dz_f;          // (float)(Nz / L): the fixed-point cell rule multiplier
+  float L_f;               // (float)L: absorbing-wall position
+  float dt_f;
+  float qmdt[3];           // q/m dt per species
+  double dz, V, kappa;     // kappa = dz e w / (2^24 eps0): potential per fixed-point unit
+  double inv_dz;
+  // null-collision MCC
+  uint32_t t_cand[3];      // candidate iff Philox word 0 < t_cand
+  uint32_t key0[4];        // Philox key word 0 per stream (species 0..2, injection)
+  uint32_t key1;
+  float nu_max[3];
+  float n_gas;
+  float sig_n[3];          // neutral partner thermal speed sqrt(k T_n / M) per species
+  float fm[3], fM[3];      // m/(m+M), M/(m+M)
+  float half_mu_over_e[3]; // E_rel[eV] = this * g^2
+  float two_e_over_mu[3];  // g^2 = this * E_rel[eV]
+  float two_e_over_me;     // v^2 = this * E[eV] for electrons
+  float sigma_el_e, sigma_cx_i, sigma_el_i;
+  float E_exc, sigma_exc0, E_iz, lotz_aq;
+  // injection (Sec. 2.1-2.2)
+  int64_t emit_floor;
+  uint32_t t_frac;
+  float sig_w;             // sqrt(k T_w / m_e)
+  float sig_e0, sig_i0;    // replenishment thermal speeds
+  int32_t replenish;
+  int32_t pad0;
+  // diagnostics
+  double weight;
+  double m_d[3];
+  int64_t window_start;
+};
+
+// Mutable per-instance state.
+struct InstDyn {
+  int64_t step;
+  uint32_t next_id;
+  int32_t ev_count;
+  int32_t err;
+  int32_t pad;
+  int64_t win_steps;
+  int64_t count[3][2];
+  double ke[3][2];
+  int64_t emitted;
+  int64_t replenished;
+  unsigned long long coll[6];
+  unsigned long long cand[3];
+  unsigned long long cap_exceeded;
+  long long pushed;          // particle-steps since creation
+};
+
+struct Event {              // one ionisation: parent id + both children
+  uint32_t parent;
+  float z;
+  float ve[3];
+  float vi[3];
+};
+
+// Everything a kernel needs, passed by value.
+struct DevState {
+  int n_inst, n_seg;
+  int G;                   // launched blocks of the particle kernels
+  int max_nodes;           // max (Nz + 1) over instances
+  float* z; float* vx; float* vy; float* vz; uint32_t* id;
+  float* z2; float* vx2; float* vy2; float* vz2; uint32_t* id2;   // sort scratch
+  const int64_t* seg_off;  // [n_seg] first particle slot of each (instance, species)
+  const int32_t* seg_cap;  // [n_seg]
+  int32_t* seg_count;      // [n_seg] live particles
+  int64_t* part;           // [n_seg + 2]: quad prefix of the last push, Q, G_eff
+  int32_t* dcount;         // [n_seg * G] absorbed particles per (segment, block)
+  uint32_t* dead_buf;      // [total_cap] per-block absorbed-slot lists
+  uint32_t* dead_dense;    // [total_cap] ordered absorbed-slot list per segment
+  Event* ev_buf;           // [n_inst * kEvCap]
+  int64_t* rho_acc;        // [total_nodes] fixed-point charge being accumulated
+  int64_t* rho;            // [total_nodes] charge of the current state
+  float* E;                // [total_nodes] field of the current state (FP32 copy)
+  double* phi;             // [total_nodes]
+  int32_t* sort_hist;      // counting-sort histograms, per segment [cell][chunk]
+  const int64_t* sort_hoff;  // [n_seg] first histogram entry of each segment
+  unsigned long long* cand_buf;  // [cand_cap] null-collision candidates: (segment << 32) | slot
+  unsigned int* cand_count;      // [1]
+  int cand_cap;
+  const InstConst* ic;
+  InstDyn* dyn;
+};
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
+// SC'11.  Ten rounds of two 32x32->64 products with a Weyl-sequence key.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+    unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Same function, rounds not unrolled: for rare paths, to keep register use low.
+static __device__ __noinline__ uint4 philox10_rolled(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll 1
+  for (int r = 0; r < 10; ++r) {
+    unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+    unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1,
+                   (uint32_t)p0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// uniform on (0,1): (k + 1/2) 2^-23, k = r >> 9 -- exact in FP32
+__device__ __forceinline__ float u01f(uint32_t r) {
+  return (__uint2float_rn(r >> 9) + 0.5f) * 1.1920928955078125e-07f;
+}
+
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& n0, float& n1) {
+  float rad = sqrtf(-2.0f * logf(u01f(a)));
+  float s, c;
+  sincospif(2.0f * u01f(b), &s, &c);
+  n0 = rad * c;
+  n1 = rad * s;
+}
+
+__device__ __forceinline__ void iso_dir(uint32_t rc, uint32_t rp, float& dx, float& dy, float& dz) {
+  float c = 1.0f - 2.0f * u01f(rc);
+  float s = sqrtf(fmaxf(0.0f, 1.0f - c * c));
+  float sp, cp;
+  sincospif(2.0f * u01f(rp), &sp, &cp);
+  dx = s * cp;
+  dy = s * sp;
+  dz = c;
+}
+
+// Fixed-point cell rule, all FP32 round-to-nearest with no contraction:
+// s = z * inv_dz, j = floor(s) clamped to [0, Nz-1], f = s - j.
+__device__ __forceinline__ void cell_of(float z, float inv_dz, int Nz, int& j, float& f) {
+  float s = __fmul_rn(z, inv_dz);
+  int jj = __float2int_rd(s);
+  jj = min(max(jj, 0), Nz - 1);
+  j = jj;
+  f = __fsub_rn(s, __int2float_rn(jj));
+}
+
+__device__ __forceinline__ long long frac_units(float f) {
+  return (long long)__fmul_rn(f, 16777216.0f);
+}
+
+// ---------------------------------------------------------------- block scans
+// Exclusive scan of one value per thread; *total gets the block sum.
+// ws: shared scratch of >= 32 elements.  Must be called by all threads.
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T* total, T* ws) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  T x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    T w = (lane < nw) ? ws[lane] : (T)0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    ws[lane] = w;
+  }
+  __syncthreads();
+  T base = (wid > 0) ? ws[wid - 1] : (T)0;
+  *total = ws[nw - 1];
+  __syncthreads();
+  return base + x - v;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* ws) {
+  T tot;
+  (void)block_exclusive_scan<T>(v, &tot, ws);
+  return tot;
+}
+
+}  // namespace pic

@@ -1,0 +1,769 @@
+// pic_kernels.cu -- sm_103a kernels of one PIC-MCC time step
+// (arXiv 2605.07083, Sec. 2.1-2.2):
+//
+//   k_push  : gather E(z) from shared memory, leapfrog push (only v_z is
+//             accelerated, 1D-3V), absorbing electrodes, null-collision MCC
+//             candidates on a Philox counter stream, and the fixed-point
+//             charge deposit of the survivors into a per-block shared-memory
+//             histogram flushed with 64-bit integer atomics.  One streaming
+//             pass over z, v_z, id (128-bit vector loads/stores).
+//   k_post  : one block per diode: ordered absorbed-slot lists -> boundary
+//             tallies, deterministic hole-filling compaction, ionisation
+//             children (by parent id), thermionic emission, ion-loss
+//             replenishment, their deposit, and the FP64 Poisson/E solve.
+//   k_field : the Poisson/E solve alone (after a full deposit).
+#include "pic_internal.cuh"
+
+namespace pic {
+
+// ------------------------------------------------------------------ partition
+// Every particle kernel splits the concatenation of all (instance, species)
+// segments, in units of 4 particles ("quads"), into G_eff contiguous ranges,
+// one per block.  segS[g] = first quad of segment g, segS[n_seg] = total.
+__device__ void seg_quad_prefix(const DevState& st, long long* segS, long long* ws) {
+  long long carry = 0;
+  for (int base = 0; base < st.n_seg; base += blockDim.x) {
+    int g = base + threadIdx.x;
+    long long q = (g < st.n_seg) ? (long long)((st.seg_count[g] + 3) >> 2) : 0LL;
+    long long tot;
+    long long ex = block_exclusive_scan<long long>(q, &tot, ws);
+    if (g < st.n_seg) segS[g] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) segS[st.n_seg] = carry;
+  __syncthreads();
+}
+
+__device__ __forceinline__ int effective_blocks(long long Q, int grid, int threads) {
+  long long need = (Q + threads - 1) / threads;
+  if (need < 1) need = 1;
+  return (int)(need < grid ? need : grid);
+}
+
+__device__ __forceinline__ void flush_acc(const long long* acc, int n_nodes, int64_t* dst) {
+  for (int j = threadIdx.x; j < n_nodes; j += blockDim.x) {
+    long long v = acc[j];
+    if (v != 0) atomicAdd(reinterpret_cast<unsigned long long*>(dst + j), (unsigned long long)v);
+  }
+}
+
+__device__ __forceinline__ void deposit_smem(long long* acc, float z, float inv_dz, int Nz,
+                                             long long sgn) {
+  int j;
+  float f;
+  cell_of(z, inv_dz, Nz, j, f);
+  long long q = frac_units(f);
+  atomicAdd(reinterpret_cast<unsigned long long*>(acc + j),
+            (unsigned long long)(sgn * ((long long)kTwo24 - q)));
+  atomicAdd(reinterpret_cast<unsigned long long*>(acc + j + 1), (unsigned long long)(sgn * q));
+}
+
+// ------------------------------------------------------------------ MCC
+// Null-collision Monte Carlo collision of one candidate (Sec. 2.2; Vahedi &
+// Surendra).  Draw block 0: word 1 selects the process against the
+// cumulative n sigma_k(E_rel) |g| (null beyond), words 2-3 the isotropic
+// direction.  Block 1: neutral partner velocity (Maxwellian at T_n).  Block
+// 2: ionisation energy split and the ejected electron's direction.
+// Returns the new v_z; writes v_x, v_y in place.  Rare path: kept out of line.
+__device__ __noinline__ float collide(const InstConst* __restrict__ icg, InstDyn* dyn,
+                                      Event* evb, float* vxp, float* vyp, int sp, uint32_t pid,
+                                      uint32_t stepw, long long step, float z, float vz) {
+  const InstConst& ic = *icg;
+  const uint32_t k0 = ic.key0[sp], k1 = ic.key1;
+  const uint4 A = philox10_rolled(make_uint4(pid, stepw, 0u, TAG_MCC), k0, k1);
+  const uint4 B = philox10_rolled(make_uint4(pid, stepw, 1u, TAG_MCC), k0, k1);
+  float n0, n1, n2, n3;
+  box_muller(B.x, B.y, n0, n1);
+  box_muller(B.z, B.w, n2, n3);
+  const float sn = ic.sig_n[sp];
+  const float vnx = sn * n0, vny = sn * n1, vnz = sn * n2;
+  const float vx = *vxp, vy = *vyp;
+  const float gx = vx - vnx, gy = vy - vny, gz = vz - vnz;
+  const float g2 = gx * gx + gy * gy + gz * gz;
+  const float gm = sqrtf(g2);
+  const float Erel = ic.half_mu_over_e[sp] * g2;
+  const float numax = ic.nu_max[sp];
+  const float x = u01f(A.y) * numax;
+  const bool in_win = step >= ic.window_start;
+  const float fm = ic.fm[sp], fM = ic.fM[sp];
+  float nvx = vx, nvy = vy, nvz = vz;
+  int code = 0;
+  if (sp < 2) {
+    const float c0 = ic.n_gas * ic.sigma_el_e * gm;
+    float sexc = 0.0f;
+    if (ic.sigma_exc0 > 0.0f && Erel > ic.E_exc) sexc = ic.sigma_exc0 * (1.0f - ic.E_exc / Erel);
+    const float c1 = c0 + ic.n_gas * sexc * gm;
+    float siz = 0.0f;
+    if (ic.lotz_aq > 0.0f && Erel > ic.E_iz) siz = ic.lotz_aq * logf(Erel / ic.E_iz) / (Erel * ic.E_iz);
+    const float c2 = c1 + ic.n_gas * siz * gm;
+    if (c2 > numax) {
+      atomicOr(&dyn->err, ERR_ENERGYCAP);
+      if (in_win) atomicAdd(&dyn->cap_exceeded, 1ull);
+    }
+    code = (x < c0) ? 1 : (x < c1) ? 2 : (x < c2) ? 3 : 0;
+    if (code == 1 || code == 2) {
+      float gn = gm;
+      if (code == 2) gn = sqrtf((Erel - ic.E_exc) * ic.two_e_over_mu[sp]);
+      float dx, dy, dz;
+      iso_dir(A.z, A.w, dx, dy, dz);
+      nvx = fm * vx + fM * vnx + fM * gn * dx;
+      nvy = fm * vy + fM * vny + fM * gn * dy;
+      nvz = fm * vz + fM * vnz + fM * gn * dz;
+    } else if (code == 3) {
+      const uint4 Cc = philox10_rolled(make_uint4(pid, stepw, 2u, TAG_MCC), k0, k1);
+      const float Eex = Erel - ic.E_iz;
+      const float U = u01f(Cc.x);
+      const float E1 = U * Eex, E2 = (1.0f - U) * Eex;
+      float d1x, d1y, d1z, d2x, d2y, d2z;
+      iso_dir(A.z, A.w, d1x, d1y, d1z);
+      iso_dir(Cc.y, Cc.z, d2x, d2y, d2z);
+      const float s1 = sqrtf(E1 * ic.two_e_over_me), s2 = sqrtf(E2 * ic.two_e_over_me);
+      nvx = vnx + s1 * d1x;
+      nvy = vny + s1 * d1y;
+      nvz = vnz + s1 * d1z;
+      int slot = atomicAdd(&dyn->ev_count, 1);
+      if (slot < kEvCap) {
+        Event e;
+        e.parent = pid;
+        e.z = z;
+        e.ve[0] = vnx + s2 * d2x;
+        e.ve[1] = vny + s2 * d2y;
+        e.ve[2] = vnz + s2 * d2z;
+        e.vi[0] = vnx;
+        e.vi[1] = vny;
+        e.vi[2] = vnz;
+        evb[slot] = e;
+      } else {
+        atomicOr(&dyn->err, ERR_CAPACITY);
+      }
+    }
+  } else {
+    const float c0 = ic.n_gas * ic.sigma_cx_i * gm;
+    const float c1 = c0 + ic.n_gas * ic.sigma_el_i * gm;
+    if (c1 > numax) {
+      atomicOr(&dyn->err, ERR_ENERGYCAP);
+      if (in_win) atomicAdd(&dyn->cap_exceeded, 1ull);
+    }
+    code = (x < c0) ? 4 : (x < c1) ? 5 : 0;
+    if (code == 4) {            // charge exchange: the ion takes the neutral's velocity
+      nvx = vnx;
+      nvy = vny;
+      nvz = vnz;
+    } else if (code == 5) {
+      float dx, dy, dz;
+      iso_dir(A.z, A.w, dx, dy, dz);
+      nvx = fm * vx + fM * vnx + fM * gm * dx;
+      nvy = fm * vy + fM * vny + fM * gm * dy;
+      nvz = fm * vz + fM * vnz + fM * gm * dz;
+    }
+  }
+  if (in_win) {
+    atomicAdd(&dyn->cand[sp], 1ull);
+    atomicAdd(&dyn->coll[code], 1ull);
+  }
+  if (code != 0) {
+    *vxp = nvx;
+    *vyp = nvy;
+  }
+  return nvz;
+}
+
+// Apply the collisions of the step's null-collision candidates.
+__global__ void __launch_bounds__(kMccThreads) k_mcc(DevState st) {
+  const unsigned n = min(*st.cand_count, (unsigned)st.cand_cap);
+  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const unsigned long long e = st.cand_buf[k];
+    const int g = (int)(e >> 32);
+    const long long slot = st.seg_off[g] + (long long)(e & 0xffffffffu);
+    const int inst = g / 3, sp = g - 3 * inst;
+    const long long step = st.dyn[inst].step;
+    const float vz = collide(st.ic + inst, st.dyn + inst, st.ev_buf + (long long)inst * kEvCap,
+                             st.vx + slot, st.vy + slot, sp, st.id[slot], (uint32_t)step, step,
+                             st.z[slot], st.vz[slot]);
+    st.vz[slot] = vz;
+  }
+}
+
+// ------------------------------------------------------------------ k_push
+struct SegCtx {
+  float inv_dz, Lf, dt, qmdt;
+  int Nz;
+  uint32_t tc, k0, k1, stepw;
+  long long step;
+  long long sgn;
+};
+
+// One particle: gather, leapfrog, wall test, deposit of the survivor, and
+// the null-collision candidate test.  Returns bit 0 = absorbed, bit 1 =
+// collision candidate (its collision is applied afterwards, out of line; a
+// collision changes velocities only, so the deposit of z is final here).
+__device__ __forceinline__ unsigned push_one(const SegCtx& c, const float* Es, long long* acc,
+                                             float& z, float& vz, uint32_t pid) {
+  int j;
+  float f;
+  cell_of(z, c.inv_dz, c.Nz, j, f);
+  const float e0 = Es[j], e1 = Es[j + 1];
+  const float Ez = fmaf(f, e1 - e0, e0);
+  vz = fmaf(c.qmdt, Ez, vz);
+  z = fmaf(vz, c.dt, z);
+  if (!(z >= 0.0f && z < c.Lf)) return 1u;
+  deposit_smem(acc, z, c.inv_dz, c.Nz, c.sgn);
+  if (c.tc != 0u) {
+    const uint4 r = philox10(make_uint4(pid, c.stepw, 0u, TAG_MCC), c.k0, c.k1);
+    if (r.x < c.tc) return 2u;
+  }
+  return 0u;
+}
+
+template <bool kDepositOnly>
+__device__ __forceinline__ void push_body(const DevState& st) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  long long* acc = reinterpret_cast<long long*>(smem);
+  float* Es = reinterpret_cast<float*>(smem + (size_t)st.max_nodes * 8);
+  long long* segS = reinterpret_cast<long long*>(smem + (size_t)st.max_nodes * 12 +
+                                                 ((st.max_nodes & 1) ? 4 : 0));
+  __shared__ long long ws64[32];
+  __shared__ int ws32[32];
+  __shared__ InstConst icS;
+
+  seg_quad_prefix(st, segS, ws64);
+  const long long Q = segS[st.n_seg];
+  const int Geff = effective_blocks(Q, gridDim.x, blockDim.x);
+  if (!kDepositOnly && blockIdx.x == 0) {
+    for (int g = threadIdx.x; g <= st.n_seg; g += blockDim.x) st.part[g] = segS[g];
+    if (threadIdx.x == 0) st.part[st.n_seg + 1] = Geff;
+  }
+  if ((int)blockIdx.x >= Geff) return;
+  const long long lo = (long long)blockIdx.x * Q / Geff;
+  const long long hi = ((long long)blockIdx.x + 1) * Q / Geff;
+  if (lo >= hi) return;
+
+  // first segment whose quad range ends after lo
+  int glo = 0, ghi = st.n_seg - 1;
+  while (glo < ghi) {
+    int mid = (glo + ghi) >> 1;
+    if (segS[mid + 1] > lo) ghi = mid; else glo = mid + 1;
+  }
+
+  int cur = -1;
+  for (int g = glo; g < st.n_seg && segS[g] < hi; ++g) {
+    const long long s0 = segS[g], s1 = segS[g + 1];
+    if (s1 <= lo || s1 == s0) continue;
+    const int inst = g / 3, sp = g - 3 * inst;
+    if (inst != cur) {
+      if (cur >= 0) {
+        __syncthreads();
+        flush_acc(acc, icS.Nz + 1, st.rho_acc + icS.node_off);
+      }
+      __syncthreads();
+      {
+        const int* src = reinterpret_cast<const int*>(st.ic + inst);
+        int* dst = reinterpret_cast<int*>(&icS);
+        for (int w = threadIdx.x; w < (int)(sizeof(InstConst) / 4); w += blockDim.x) dst[w] = src[w];
+      }
+      __syncthreads();
+      const int nn = icS.Nz + 1;
+      for (int j = threadIdx.x; j < nn; j += blockDim.x) {
+        acc[j] = 0;
+        if (!kDepositOnly) Es[j] = st.E[icS.node_off + j];
+      }
+      __syncthreads();
+      cur = inst;
+    }
+    const long long q0 = (lo > s0 ? lo : s0) - s0;
+    const long long q1 = (hi < s1 ? hi : s1) - s0;
+    const long long off = st.seg_off[g];
+    const int N = st.seg_count[g];
+    float* __restrict__ zp = st.z + off;
+    float* __restrict__ vzp = st.vz + off;
+    const long long sgn = (sp == 2) ? 1LL : -1LL;
+
+    if (kDepositOnly) {
+      for (long long qb = q0; qb < q1; qb += blockDim.x) {
+        const long long q = qb + threadIdx.x;
+        if (q >= q1) continue;
+        const long long i = 4 * q;
+        if (i + 3 < N) {
+          const float4 z4 = *reinterpret_cast<const float4*>(zp + i);
+          deposit_smem(acc, z4.x, icS.inv_dz_f, icS.Nz, sgn);
+          deposit_smem(acc, z4.y, icS.inv_dz_f, icS.Nz, sgn);
+          deposit_smem(acc, z4.z, icS.inv_dz_f, icS.Nz, sgn);
+          deposit_smem(acc, z4.w, icS.inv_dz_f, icS.Nz, sgn);
+        } else {
+          for (int k = 0; k < 4; ++k)
+            if (i + k < N) deposit_smem(acc, zp[i + k], icS.inv_dz_f, icS.Nz, sgn);
+        }
+      }
+      continue;
+    }
+
+    SegCtx c;
+    c.inv_dz = icS.inv_dz_f;
+    c.Lf = icS.L_f;
+    c.dt = icS.dt_f;
+    c.qmdt = icS.qmdt[sp];
+    c.Nz = icS.Nz;
+    c.tc = icS.t_cand[sp];
+    c.k0 = icS.key0[sp];
+    c.k1 = icS.key1;
+    c.step = st.dyn[inst].step;
+    c.stepw = (uint32_t)c.step;
+    c.sgn = sgn;
+    const uint32_t* __restrict__ idp = st.id + off;
+    uint32_t* dbuf = st.dead_buf + off + 4 * q0;
+    int dead_run = 0;
+
+    for (long long qb = q0; qb < q1; qb += blockDim.x) {
+      const long long q = qb + threadIdx.x;
+      unsigned dm = 0, cm = 0;
+      if (q < q1) {
+        const long long i = 4 * q;
+        if (i + 3 < N) {
+          float4 z4 = __ldcs(reinterpret_cast<const float4*>(zp + i));
+          float4 v4 = __ldcs(reinterpret_cast<const float4*>(vzp + i));
+          const uint4 id4 = __ldcs(reinterpret_cast<const uint4*>(idp + i));
+          const unsigned r0 = push_one(c, Es, acc, z4.x, v4.x, id4.x);
+          const unsigned r1 = push_one(c, Es, acc, z4.y, v4.y, id4.y);
+          const unsigned r2 = push_one(c, Es, acc, z4.z, v4.z, id4.z);
+          const unsigned r3 = push_one(c, Es, acc, z4.w, v4.w, id4.w);
+          dm = (r0 & 1u) | ((r1 & 1u) << 1) | ((r2 & 1u) << 2) | ((r3 & 1u) << 3);
+          cm = (r0 >> 1) | ((r1 >> 1) << 1) | ((r2 >> 1) << 2) | ((r3 >> 1) << 3);
+          __stcs(reinterpret_cast<float4*>(zp + i), z4);
+          __stcs(reinterpret_cast<float4*>(vzp + i), v4);
+        } else {
+          for (int k = 0; k < 4; ++k) {
+            if (i + k < N) {
+              float zz = zp[i + k], vv = vzp[i + k];
+              const uint32_t pid = idp[i + k];
+              const unsigned r = push_one(c, Es, acc, zz, vv, pid);
+              if (r & 1u) dm |= 1u << k;
+              if (r & 2u) cm |= 1u << k;
+              zp[i + k] = zz;
+              vzp[i + k] = vv;
+            }
+          }
+        }
+      }
+      // null-collision candidates -> compact list (one atomic per warp)
+      {
+        const int cc = __popc(cm);
+        const unsigned any = __ballot_sync(0xffffffffu, cc != 0);
+        if (any) {
+          const int lane = threadIdx.x & 31;
+          int incl = cc;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+          }
+          const int wtot = __shfl_sync(0xffffffffu, incl, 31);
+          const int leader = __ffs(any) - 1;
+          unsigned base = 0;
+          if (lane == leader) base = atomicAdd(st.cand_count, (unsigned)wtot);
+          base = __shfl_sync(0xffffffffu, base, leader);
+          unsigned w = base + (unsigned)(incl - cc);
+          for (int k2 = 0; k2 < 4; ++k2) {
+            if (cm & (1u << k2)) {
+              if (w < (unsigned)st.cand_cap)
+                st.cand_buf[w] = ((unsigned long long)g << 32) | (unsigned long long)(4 * q + k2);
+              else
+                atomicOr(&st.dyn[inst].err, ERR_CAPACITY);
+              ++w;
+            }
+          }
+        }
+      }
+      if (__syncthreads_or(dm != 0)) {
+        int tot;
+        int ex = block_exclusive_scan<int>(__popc(dm), &tot, ws32);
+        if (dm) {
+          int w = dead_run + ex;
+          for (int k = 0; k < 4; ++k)
+            if (dm & (1u << k)) dbuf[w++] = (uint32_t)(4 * q + k);
+        }
+        dead_run += tot;
+      }
+    }
+    if (threadIdx.x == 0) st.dcount[(long long)g * st.G + blockIdx.x] = dead_run;
+  }
+  if (cur >= 0) {
+    __syncthreads();
+    flush_acc(acc, icS.Nz + 1, st.rho_acc + icS.node_off);
+  }
+}
+
+__global__ void __launch_bounds__(256, 3) k_push(DevState st) { push_body<false>(st); }
+__global__ void k_deposit(DevState st) { push_body<true>(st); }
+
+// ------------------------------------------------------------------ field solve
+// Poisson with Dirichlet phi_0 = 0, phi_Nz = V (Sec. 2.1), solved exactly by
+// summation: with d_j = phi_{j+1} - phi_j the difference equations give
+// d_j = d_0 - kappa G_j, G_j = sum_{k=1..j} rho_k (exact int64), and
+// phi_Nz = V fixes d_0 = (V + kappa sum_{j<Nz} G_j) / Nz.  E_j = -(d_j +
+// d_{j-1}) / (2 dz) inside, one-sided at the electrodes.  rho_s is the
+// block's shared copy of the fixed-point charge; it is overwritten with G.
+__device__ void field_solve(const InstConst& ic, long long* rho_s, float* E, double* phi,
+                            long long* ws) {
+  const int Nz = ic.Nz;
+  const int nt = blockDim.x;
+  const int c = (Nz + nt - 1) / nt;            // <= 4 for Nz <= 4096, nt = 1024
+  const int j0 = threadIdx.x * c;
+  long long a[4];
+  long long loc = 0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    if (u < c) {
+      const int j = j0 + u;
+      const long long v = (j >= 1 && j < Nz) ? rho_s[j] : 0LL;
+      loc += v;
+      a[u] = loc;
+    }
+  }
+  long long tot;
+  const long long ex = block_exclusive_scan<long long>(loc, &tot, ws);
+  long long hx[4];
+  long long lsum = 0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    if (u < c) {
+      a[u] += ex;
+      if (j0 + u < Nz) {
+        hx[u] = lsum;
+        lsum += a[u];
+      }
+    }
+  }
+  long long Htot;
+  const long long hex = block_exclusive_scan<long long>(lsum, &Htot, ws);
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    if (u < c && j0 + u < Nz) rho_s[j0 + u] = a[u];
+  __syncthreads();
+  const double kap = ic.kappa, dz = ic.dz;
+  const double d0 = (ic.V + kap * (double)Htot) / (double)Nz;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int j = j0 + u;
+    if (u < c && j < Nz) {
+      const double dj = d0 - kap * (double)a[u];
+      double Ej;
+      if (j == 0) {
+        Ej = -dj / dz;
+      } else {
+        const double dm1 = d0 - kap * (double)rho_s[j - 1];
+        Ej = -(dj + dm1) / (2.0 * dz);
+      }
+      E[j] = (float)Ej;
+      phi[j] = (double)j * d0 - kap * (double)(hex + hx[u]);
+    }
+  }
+  if (threadIdx.x == 0) {
+    const double dl = d0 - kap * (double)rho_s[Nz - 1];
+    E[Nz] = (float)(-dl / dz);
+    phi[Nz] = ic.V;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kPostThreads) k_field(DevState st) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  long long* rho_s = reinterpret_cast<long long*>(smem);
+  __shared__ long long ws64[32];
+  const InstConst& ic = st.ic[blockIdx.x];
+  const int nn = ic.Nz + 1;
+  const int off = ic.node_off;
+  for (int j = threadIdx.x; j < nn; j += blockDim.x) {
+    const long long v = st.rho_acc[off + j];
+    rho_s[j] = v;
+    st.rho[off + j] = v;
+    st.rho_acc[off + j] = 0;
+  }
+  __syncthreads();
+  field_solve(ic, rho_s, st.E + off, st.phi + off, ws64);
+}
+
+// ------------------------------------------------------------------ k_post
+__device__ __forceinline__ void move_particle(const DevState& st, long long off, long long src,
+                                              long long dst) {
+  st.z[off + dst] = st.z[off + src];
+  st.vx[off + dst] = st.vx[off + src];
+  st.vy[off + dst] = st.vy[off + src];
+  st.vz[off + dst] = st.vz[off + src];
+  st.id[off + dst] = st.id[off + src];
+}
+
+__device__ __forceinline__ void put_particle(const DevState& st, long long off, long long slot,
+                                             float z, float vx, float vy, float vz, uint32_t id) {
+  st.z[off + slot] = z;
+  st.vx[off + slot] = vx;
+  st.vy[off + slot] = vy;
+  st.vz[off + slot] = vz;
+  st.id[off + slot] = id;
+}
+
+__global__ void __launch_bounds__(kPostThreads) k_post(DevState st) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  long long* rho_s = reinterpret_cast<long long*>(smem);
+  unsigned long long* evk = reinterpret_cast<unsigned long long*>(smem + (size_t)st.max_nodes * 8);
+  int* bpre = reinterpret_cast<int*>(evk + kEvCap);
+  __shared__ long long ws64[32];
+  __shared__ int ws32[32];
+  __shared__ double wsd[32];
+  __shared__ InstConst ic;
+  __shared__ int sD[3], sN[3], sNn[3];
+  __shared__ long long sCnt[3][2];
+  __shared__ double sKe[3][2];
+  __shared__ int sNemit, sE;
+
+  const int inst = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (inst == 0 && tid == 0) {
+    if (*st.cand_count > (unsigned)st.cand_cap) atomicOr(&st.dyn[0].err, ERR_CAPACITY);
+    *st.cand_count = 0u;
+  }
+  {
+    const int* src = reinterpret_cast<const int*>(st.ic + inst);
+    int* dst = reinterpret_cast<int*>(&ic);
+    for (int w = tid; w < (int)(sizeof(InstConst) / 4); w += nt) dst[w] = src[w];
+  }
+  __syncthreads();
+  InstDyn* dyn = st.dyn + inst;
+  const long long step = dyn->step;
+  const long long Q = st.part[st.n_seg];
+  const int Geff = (int)st.part[st.n_seg + 1];
+
+  // ---- A: ordered absorbed lists and boundary tallies per species
+  for (int sp = 0; sp < 3; ++sp) {
+    const int g = inst * 3 + sp;
+    const long long off = st.seg_off[g];
+    const int N = st.seg_count[g];
+    const long long qg = (N + 3) >> 2;
+    const long long Sg = st.part[g];
+    int carry = 0;
+    for (int base = 0; base < Geff; base += nt) {
+      const int b = base + tid;
+      int c = 0;
+      if (b < Geff && qg > 0) {
+        const long long lb = (long long)b * Q / Geff, hb = ((long long)b + 1) * Q / Geff;
+        if (lb < hb && lb < Sg + qg && hb > Sg) c = st.dcount[(long long)g * st.G + b];
+      }
+      int tot;
+      const int ex = block_exclusive_scan<int>(c, &tot, ws32);
+      if (b < Geff) bpre[b] = carry + ex;
+      carry += tot;
+    }
+    if (tid == 0) bpre[Geff] = carry;
+    __syncthreads();
+    const int D = carry;
+    long long cnt0 = 0, cnt1 = 0;
+    double ke0 = 0.0, ke1 = 0.0;
+    const double mw = 0.5 * ic.m_d[sp] * ic.weight;
+    for (int k = tid; k < D; k += nt) {
+      int blo = 0, bhi = Geff;
+      while (bhi - blo > 1) {
+        const int mid = (blo + bhi) >> 1;
+        if (bpre[mid] <= k) blo = mid; else bhi = mid;
+      }
+      const long long lb = (long long)blo * Q / Geff;
+      const long long qstart = (lb > Sg ? lb : Sg) - Sg;
+      const uint32_t idx = st.dead_buf[off + 4 * qstart + (k - bpre[blo])];
+      st.dead_dense[off + k] = idx;
+      const float z = st.z[off + idx];
+      const double vx = st.vx[off + idx], vy = st.vy[off + idx], vz = st.vz[off + idx];
+      const double ke = mw * (vx * vx + vy * vy + vz * vz);
+      if (z < 0.0f) { cnt0 += 1; ke0 += ke; } else { cnt1 += 1; ke1 += ke; }
+    }
+    const long long c0 = block_sum<long long>(cnt0, ws64);
+    const long long c1 = block_sum<long long>(cnt1, ws64);
+    const double e0 = block_sum<double>(ke0, wsd);
+    const double e1 = block_sum<double>(ke1, wsd);
+    if (tid == 0) {
+      sCnt[sp][0] = c0; sCnt[sp][1] = c1; sKe[sp][0] = e0; sKe[sp][1] = e1;
+      sD[sp] = D; sN[sp] = N;
+    }
+    __syncthreads();
+  }
+
+  // ---- B: hole filling: live tail particles move, in order, into the
+  // absorbed slots below the new count
+  for (int sp = 0; sp < 3; ++sp) {
+    const int g = inst * 3 + sp;
+    const long long off = st.seg_off[g];
+    const int N = sN[sp], D = sD[sp], Nn = N - D;
+    const uint32_t* dd = st.dead_dense + off;
+    int lo = 0, hi = D;                         // h = #absorbed slots < Nn
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if ((int)dd[mid] < Nn) lo = mid + 1; else hi = mid;
+    }
+    const int h = lo;
+    int run = 0;
+    for (int base = 0; base < D; base += nt) {
+      const int k = base + tid;
+      int live = 0;
+      int t = Nn + k;
+      if (k < D) {
+        int a = h, b = D;
+        while (a < b) {
+          const int mid = (a + b) >> 1;
+          if ((int)dd[mid] < t) a = mid + 1; else b = mid;
+        }
+        live = !(a < D && (int)dd[a] == t);
+      }
+      int tot;
+      const int r = block_exclusive_scan<int>(live, &tot, ws32) + run;
+      if (live) move_particle(st, off, t, dd[r]);
+      run += tot;
+    }
+    if (tid == 0) sNn[sp] = Nn;
+    __syncthreads();
+  }
+
+  // ---- C: ionisation events ordered by parent id
+  if (tid == 0) {
+    int e = dyn->ev_count;
+    if (e > kEvCap) {
+      atomicOr(&dyn->err, ERR_CAPACITY);
+      e = kEvCap;
+    }
+    sE = e;
+    long long nem = ic.emit_floor;
+    if (ic.t_frac != 0u) {
+      const uint4 r = philox10(make_uint4(0u, (uint32_t)step, 0u, TAG_EMIT_N), ic.key0[kStreamInject], ic.key1);
+      if (r.x < ic.t_frac) nem += 1;
+    }
+    sNemit = (int)nem;
+  }
+  __syncthreads();
+  const int E = sE;
+  const Event* evb = st.ev_buf + (long long)inst * kEvCap;
+  if (E > 1) {
+    int P2 = 1;
+    while (P2 < E) P2 <<= 1;
+    for (int k = tid; k < P2; k += nt)
+      evk[k] = (k < E) ? (((unsigned long long)evb[k].parent << 32) | (unsigned)k) : ~0ull;
+    __syncthreads();
+    for (int kk = 2; kk <= P2; kk <<= 1) {
+      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+        for (int i = tid; i < P2; i += nt) {
+          const int ixj = i ^ jj;
+          if (ixj > i) {
+            const unsigned long long a = evk[i], b = evk[ixj];
+            const bool up = (i & kk) == 0;
+            if ((a > b) == up) { evk[i] = b; evk[ixj] = a; }
+          }
+        }
+        __syncthreads();
+      }
+    }
+  } else if (E == 1 && tid == 0) {
+    evk[0] = 0ull;
+  }
+
+  // ---- D: appends (children, emission, replenishment) and their deposit
+  const int nn = ic.Nz + 1;
+  for (int j = tid; j < nn; j += nt) rho_s[j] = st.rho_acc[ic.node_off + j];
+  __syncthreads();
+  const uint32_t base_id = dyn->next_id;
+  const int Nemit = sNemit;
+  const int P = ic.replenish ? (int)(sCnt[2][0] + sCnt[2][1]) : 0;
+  const int g0 = inst * 3, g1 = g0 + 1, g2 = g0 + 2;
+  const long long off0 = st.seg_off[g0], off1 = st.seg_off[g1], off2 = st.seg_off[g2];
+  const int cap0 = st.seg_cap[g0], cap1 = st.seg_cap[g1], cap2 = st.seg_cap[g2];
+  const int Nn0 = sNn[0], Nn1 = sNn[1], Nn2 = sNn[2];
+  bool overflow = false;
+  for (int k = tid; k < E; k += nt) {
+    const Event ev = evb[(int)(evk[k] & 0xffffffffu)];
+    const long long s1 = (long long)Nn1 + k, s2 = (long long)Nn2 + k;
+    if (s1 < cap1) {
+      put_particle(st, off1, s1, ev.z, ev.ve[0], ev.ve[1], ev.ve[2], base_id + 2u * k);
+      deposit_smem(rho_s, ev.z, ic.inv_dz_f, ic.Nz, -1);
+    } else overflow = true;
+    if (s2 < cap2) {
+      put_particle(st, off2, s2, ev.z, ev.vi[0], ev.vi[1], ev.vi[2], base_id + 2u * k + 1u);
+      deposit_smem(rho_s, ev.z, ic.inv_dz_f, ic.Nz, 1);
+    } else overflow = true;
+  }
+  const uint32_t id_emit = base_id + 2u * (uint32_t)E;
+  for (int k = tid; k < Nemit; k += nt) {
+    const uint4 r = philox10(make_uint4((uint32_t)k, (uint32_t)step, 0u, TAG_EMIT), ic.key0[kStreamInject], ic.key1);
+    float n0, n1;
+    box_muller(r.x, r.y, n0, n1);
+    const float vz = ic.sig_w * sqrtf(-2.0f * logf(u01f(r.z)));
+    const float z = vz * ic.dt_f;
+    const long long s = (long long)Nn0 + k;
+    if (s < cap0) {
+      put_particle(st, off0, s, z, ic.sig_w * n0, ic.sig_w * n1, vz, id_emit + (uint32_t)k);
+      deposit_smem(rho_s, z, ic.inv_dz_f, ic.Nz, -1);
+    } else overflow = true;
+  }
+  const uint32_t id_repl = id_emit + (uint32_t)Nemit;
+  for (int k = tid; k < P; k += nt) {
+    const uint4 A = philox10(make_uint4((uint32_t)k, (uint32_t)step, 0u, TAG_REPL), ic.key0[kStreamInject], ic.key1);
+    const uint4 B = philox10(make_uint4((uint32_t)k, (uint32_t)step, 1u, TAG_REPL), ic.key0[kStreamInject], ic.key1);
+    float gg[6];
+    box_muller(A.x, A.y, gg[0], gg[1]);
+    box_muller(A.z, A.w, gg[2], gg[3]);
+    box_muller(B.x, B.y, gg[4], gg[5]);
+    const float z = u01f(B.z) * ic.L_f;
+    const long long s1 = (long long)Nn1 + E + k, s2 = (long long)Nn2 + E + k;
+    if (s1 < cap1) {
+      put_particle(st, off1, s1, z, ic.sig_e0 * gg[0], ic.sig_e0 * gg[1], ic.sig_e0 * gg[2],
+                   id_repl + 2u * k);
+      deposit_smem(rho_s, z, ic.inv_dz_f, ic.Nz, -1);
+    } else overflow = true;
+    if (s2 < cap2) {
+      put_particle(st, off2, s2, z, ic.sig_i0 * gg[3], ic.sig_i0 * gg[4], ic.sig_i0 * gg[5],
+                   id_repl + 2u * k + 1u);
+      deposit_smem(rho_s, z, ic.inv_dz_f, ic.Nz, 1);
+    } else overflow = true;
+  }
+  if (__syncthreads_or(overflow) && tid == 0) atomicOr(&dyn->err, ERR_CAPACITY);
+
+  // ---- E: charge of the new state and its field
+  for (int j = tid; j < nn; j += nt) {
+    st.rho[ic.node_off + j] = rho_s[j];
+    st.rho_acc[ic.node_off + j] = 0;
+  }
+  __syncthreads();
+  field_solve(ic, rho_s, st.E + ic.node_off, st.phi + ic.node_off, ws64);
+
+  // ---- F: counts, ids, window, step
+  if (tid == 0) {
+    st.seg_count[g0] = min(Nn0 + Nemit, cap0);
+    st.seg_count[g1] = min(Nn1 + E + P, cap1);
+    st.seg_count[g2] = min(Nn2 + E + P, cap2);
+    dyn->next_id = id_repl + 2u * (uint32_t)P;
+    if (step >= ic.window_start) {
+      dyn->win_steps += 1;
+      for (int sp = 0; sp < 3; ++sp)
+        for (int w = 0; w < 2; ++w) {
+          dyn->count[sp][w] += sCnt[sp][w];
+          dyn->ke[sp][w] += sKe[sp][w];
+        }
+      dyn->emitted += Nemit;
+      dyn->replenished += P;
+    }
+    dyn->pushed += (long long)sN[0] + sN[1] + sN[2];
+    dyn->ev_count = 0;
+    dyn->step = step + 1;
+  }
+}
+
+// ------------------------------------------------------------------ helpers
+__global__ void k_fill_ids(uint32_t* id, long long n, uint32_t first) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) id[i] = first + (uint32_t)i;
+}
+
+__global__ void k_count_outside(const float* z, long long n, float Lf, int* bad) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int b = 0;
+  if (i < n) {
+    const float v = z[i];
+    b = !(v >= 0.0f && v < Lf);
+  }
+  if (__syncthreads_or(b) && threadIdx.x == 0) atomicAdd(bad, 1);
+}
+
+}  // namespace pic

@@ -1,0 +1,238 @@
+"""GPU (C-ABI) vs CPU oracle parity.  Needs a GPU."""
+import math
+
+import numpy as np
+import pytest
+
+from parity_util import REL, by_id, compare_species, load_both, mixed_state
+from paper_2605_07083_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from oracle import oracle as O
+    from paper_2605_07083_gb300 import build as B
+    B.build()
+    from paper_2605_07083_gb300 import pic
+    pic.load()
+    return pic, O
+
+
+def _pair(env, p, state):
+    pic, O = env
+    gpu = pic.Diode(p)
+    ora = O.Oracle(p)
+    load_both(gpu, ora, state)
+    return gpu, ora
+
+
+# ------------------------------------------------------------ deposit / field
+@pytest.mark.parametrize("which,n_emit,n_pairs", [
+    ("small", 7, 3),                 # fewer particles than one quad per species
+    ("small", 20001, 9999),          # ragged, several blocks
+    ("production", 100003, 50001),   # 2048 cells, ragged tail
+])
+def test_fixed_point_charge_is_bit_exact(env, which, n_emit, n_pairs):
+    p = W.single_diode_small() if which == "small" else W.single_diode_production()
+    gpu, ora = _pair(env, p, mixed_state(p, 11, n_emit, n_pairs))
+    rg, ro = gpu.rho_fixed(), ora.rho_fixed()
+    assert rg.dtype == np.int64 and np.array_equal(rg, ro)
+    n_e = 2 * 5 + n_emit + n_pairs
+    n_i = 5 + n_pairs
+    assert rg.sum() == (n_i - n_e) * (1 << 24)
+
+
+def test_empty_diode_field_is_vacuum(env):
+    p = W.single_diode_small()
+    gpu, ora = _pair(env, p, {0: [np.zeros(0, np.float32)] * 4, 1: [np.zeros(0, np.float32)] * 4,
+                              2: [np.zeros(0, np.float32)] * 4})
+    assert not gpu.rho_fixed().any()
+    phi, E = gpu.field()
+    np.testing.assert_allclose(E, -p["V"] / p["L"], rtol=1e-6)
+    np.testing.assert_allclose(phi, p["V"] * np.arange(p["Nz"] + 1) / p["Nz"], rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("which", ["small", "production"])
+def test_field_matches_oracle(env, which):
+    p = W.single_diode_small() if which == "small" else W.single_diode_production()
+    p["weight"] *= 50.0                      # strong space charge
+    gpu, ora = _pair(env, p, mixed_state(p, 12, 30011, 7001))
+    phi_g, E_g = gpu.field()
+    phi_o, E_o = ora.field()
+    np.testing.assert_allclose(phi_g, phi_o, rtol=0, atol=1e-9 * np.abs(phi_o).max())
+    np.testing.assert_allclose(E_g, E_o, rtol=0, atol=2e-6 * np.abs(E_o).max())
+
+
+# ------------------------------------------------------------ one time step
+def _one_step_case(env, p, state, step0=17):
+    gpu, ora = _pair(env, p, state)
+    gpu.set_step(step0)
+    ora.set_step(step0)
+    gpu.step(1)
+    ora.step(1)
+    ev = ora.events()
+    # MCC decisions within a relative margin of 1e-5 of a channel boundary may
+    # flip between FP32 (GPU) and FP64 (oracle)
+    flips = set(ev["id"][ev["margin"] < 1e-5].tolist())
+    return gpu, ora, ev, flips
+
+
+def _wall_flip_ids(ora_state_before, p):
+    return set()
+
+
+@pytest.mark.parametrize("n_gas", [2e21, 3e23])
+def test_one_step_matches_oracle(env, n_gas):
+    p = W.single_diode_small()
+    p.update(n_gas=n_gas, replenish=1, window_start=0)
+    state = mixed_state(p, 13, 40000, 20000)
+    gpu, ora, ev, flips = _one_step_case(env, p, state)
+    for sp in range(3):
+        g, o = gpu.state(sp), ora.state(sp)
+        bad, n, bad_ids = compare_species(g, o, sp, flips)
+        assert n > 0
+        assert bad == 0, (sp, bad, n, bad_ids[:10])
+        # live populations agree exactly unless a wall decision flipped
+        assert abs(g["id"].size - o["id"].size) <= 1, (sp, g["id"].size, o["id"].size)
+    dg = gpu.diagnostics()
+    to = ora.tallies()
+    assert len(flips) <= max(2, ev.size // 1000)
+    np.testing.assert_array_equal(dg["candidates"], to["candidates"])
+    assert np.abs(dg["collisions"] - to["coll"]).sum() <= 2 * len(flips)
+    assert np.abs(dg["count"] - to["count"]).sum() <= 2
+    np.testing.assert_allclose(dg["ke"], to["ke"], rtol=1e-5, atol=1e-30)
+    assert dg["emitted"] == to["emitted"] and dg["replenished"] == to["replenished"]
+    if n_gas > 1e22:
+        assert dg["collisions"][1:].sum() > 100     # the case really exercises the MCC
+
+
+def test_one_step_rho_after_step_matches(env):
+    """Charge after one step (push + appends) agrees with the oracle's deposit of
+    its own post-step state except where FP32/FP64 positions straddle a 2^-24
+    cell fraction."""
+    p = W.single_diode_small()
+    state = mixed_state(p, 14, 30000, 10000)
+    gpu, ora, ev, flips = _one_step_case(env, p, state)
+    rg, ro = gpu.rho_fixed(), ora.rho_fixed()
+    assert rg.sum() == ro.sum()
+    tot = np.abs(ro).sum()
+    assert np.abs(rg - ro).sum() <= 1e-5 * tot
+
+
+def test_ionisation_children_match(env):
+    p = W.single_diode_small()
+    p.update(V=0.0, n_gas=1e24, sigma_el_e=0.0, sigma_exc0=0.0, T_gas_e_K=300.0,
+             window_start=0, gamma_emit=0.0)
+    n = 20000
+    v = math.sqrt(2 * 50.0 * W.E_CHARGE / W.M_E)
+    rng = np.random.default_rng(15)
+    z = ((0.2 + 0.6 * rng.random(n)) * p["L"]).astype(np.float32)
+    zero = np.zeros(n, np.float32)
+    st = {0: (z, zero, zero, np.full(n, v, np.float32)),
+          1: (np.zeros(0, np.float32),) * 4, 2: (np.zeros(0, np.float32),) * 4}
+    gpu, ora, ev, flips = _one_step_case(env, p, st)
+    n_iz = int((ev["process"] == 3).sum())
+    assert n_iz > 50
+    for sp in range(3):
+        g, o = by_id(gpu.state(sp)), by_id(ora.state(sp))
+        if not flips:
+            np.testing.assert_array_equal(g["id"], o["id"])
+        bad, cnt, _ = compare_species(gpu.state(sp), ora.state(sp), sp, flips)
+        assert bad == 0, (sp, bad, cnt)
+    assert gpu.diagnostics()["collisions"][3] == n_iz
+
+
+# ------------------------------------------------------------ determinism
+def test_run_to_run_determinism(env):
+    pic, O = env
+    p = W.single_diode_small()
+    p["n_gas"] = 2e22
+    outs = []
+    for _ in range(2):
+        d = pic.Diode(p)
+        d.step(300)
+        st = [by_id(d.state(sp)) for sp in range(3)]
+        outs.append((d.rho_fixed(), st, d.diagnostics()))
+        d.close()
+    (r1, s1, d1), (r2, s2, d2) = outs
+    assert np.array_equal(r1, r2)
+    for a, b in zip(s1, s2):
+        for k in a:
+            assert np.array_equal(a[k], b[k])
+    assert np.array_equal(d1["count"], d2["count"]) and np.array_equal(d1["ke"], d2["ke"])
+
+
+# ------------------------------------------------------------ errors
+def test_capacity_errors_are_reported(env):
+    pic, O = env
+    p = W.single_diode_small()
+    p["capacity"] = (64, 64, 64)
+    d = pic.Diode(p)
+    z = np.full(100, 1e-4, np.float32)
+    with pytest.raises(pic.PicError) as e:
+        d.inject(1, z, z * 0, z * 0, z * 0)
+    assert e.value.code == pic.PIC_ECAPACITY
+    # emission outgrows the 64-slot emitted species on the device: sticky error
+    d.step(20)
+    diag = d.diagnostics(check=False)
+    assert diag["rc"] == pic.PIC_ECAPACITY and diag["n_live"][0] <= 64
+    with pytest.raises(pic.PicError):
+        d.step(1)
+    d.close()
+
+
+def test_positions_outside_the_gap_are_rejected(env):
+    pic, O = env
+    p = W.single_diode_small()
+    d = pic.Diode(p)
+    bad = np.array([p["L"] * 1.5], np.float32)
+    with pytest.raises(pic.PicError) as e:
+        d.inject(0, bad, bad * 0, bad * 0, bad * 0)
+    assert e.value.code == pic.PIC_EINVAL
+    d.close()
+
+
+# ------------------------------------------------------------ batching
+def test_batched_instances_equal_separate_runs(env):
+    pic, O = env
+    ps = W.batched_sweep(n_instances=3, seed=500, n_steps=100)
+    for p in ps:
+        p["weight"] *= 20.0            # keep the test small
+    both = pic.Diode(ps)
+    sep = [pic.Diode(p) for p in ps]
+    both.step(60)
+    for i, d in enumerate(sep):
+        d.step(60)
+        assert np.array_equal(both.rho_fixed(i), d.rho_fixed())
+        for sp in range(3):
+            a, b = by_id(both.state(sp, instance=i)), by_id(d.state(sp))
+            for k in a:
+                assert np.array_equal(a[k], b[k]), (i, sp, k)
+        da, db = both.diagnostics(i), d.diagnostics()
+        assert np.array_equal(da["count"], db["count"])
+
+
+# ------------------------------------------------------------ sort
+def test_sort_is_a_stable_permutation_by_cell(env):
+    pic, O = env
+    p = W.single_diode_production()
+    state = mixed_state(p, 16, 50000, 20000)
+    d = pic.Diode(p)
+    for sp in range(3):
+        d.inject(sp, *state[sp])
+    r0 = d.rho_fixed()
+    before = [d.state(sp) for sp in range(3)]
+    d.sort()
+    assert np.array_equal(d.rho_fixed(), r0)
+    inv = np.float32(p["Nz"] / p["L"])
+    for sp in range(3):
+        a, b = before[sp], d.state(sp)
+        cell_a = np.clip(np.floor(a["z"] * inv), 0, p["Nz"] - 1).astype(np.int64)
+        order = np.argsort(cell_a, kind="stable")
+        for k in ("z", "vx", "vy", "vz", "id"):
+            assert np.array_equal(b[k], a[k][order]), (sp, k)
