@@ -108,8 +108,8 @@ typedef struct pic_allocator {
 /* Launch shape and scheduling knobs (pic_tune).  Zero keeps the current value. */
 typedef struct pic_tuning {
     uint32_t size;            /* sizeof(pic_tuning) */
-    int32_t push_threads;     /* threads per block of the particle kernels (64..1024, multiple of 32) */
-    int32_t push_blocks_per_sm;
+    int32_t push_threads;     /* threads per block of the particle kernels (64..256, multiple of 32) */
+    int32_t push_blocks_per_sm;  /* cap on resident blocks per SM (default: occupancy limit) */
     int32_t sort_period;      /* counting sort by cell every this many steps; < 0 disables */
     int32_t graph_steps;      /* steps captured per CUDA graph; < 0 disables graphs */
     int32_t reserved[3];
@@ -211,6 +211,10 @@ int pic_sort(pic_handle* h);
 
 /* Wait for the stream; return the first sticky error. */
 int pic_synchronize(pic_handle* h);
+
+/* Text of the first CUDA failure on this handle ("" if none): the library
+ * call site and cudaGetErrorString.  Owned by the handle. */
+const char* pic_last_error(const pic_handle* h);
 
 /* Release the handle and all device state it owns.  NULL is ignored. */
 void pic_destroy(pic_handle* h);

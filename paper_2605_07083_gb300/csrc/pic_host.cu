@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -59,7 +60,7 @@ struct pic_handle {
   int64_t total_cap = 0;
   int total_nodes = 0, max_nodes = 0;
   int sm_count = 0;
-  int push_threads = 256, blocks_per_sm = 4, G = 0;
+  int push_threads = 256, blocks_per_sm = 0, G = 0;   // 0 blocks/SM: occupancy limit
   int sort_period = 0, graph_steps = 50;
   DevState st{};
   std::vector<Alloc> allocs;
@@ -74,15 +75,20 @@ struct pic_handle {
   int mcc_blocks = 0;
   bool sort_ready = false;
   int sort_chunks = 1;
+  char last_error[256] = {0};
 };
 
 namespace {
 
-int cuda_fail(pic_handle* h, cudaError_t e) {
+int cuda_fail_at(pic_handle* h, cudaError_t e, const char* where) {
   if (e == cudaSuccess) return PIC_OK;
-  if (h && h->sticky == PIC_OK) h->sticky = PIC_ECUDA;
+  if (h && h->sticky == PIC_OK) {
+    h->sticky = PIC_ECUDA;
+    std::snprintf(h->last_error, sizeof(h->last_error), "%s: %s", where, cudaGetErrorString(e));
+  }
   return e == cudaErrorMemoryAllocation ? PIC_ENOMEM : PIC_ECUDA;
 }
+#define cuda_fail(h, e) cuda_fail_at((h), (e), __func__)
 
 void* dev_alloc(pic_handle* h, size_t bytes) {
   if (bytes == 0) bytes = 16;
@@ -137,6 +143,7 @@ InstConst derive(const pic_config& c) {
   for (int s = 0; s < 3; ++s) k.qmdt[s] = (float)(q[s] / m[s] * c.dt_s);
   k.dz = dz;
   k.inv_dz = 1.0 / dz;
+  k.inv_nz = 1.0 / c.n_cells;
   k.V = c.bias_V;
   // phi per fixed-point charge unit: dz^2 * (e w / (2^24 dz)) / eps0
   k.kappa = dz * kQe * c.weight / (16777216.0 * kEps0);
@@ -223,18 +230,7 @@ void drop_graph(pic_handle* h) {
 }
 
 int set_launch_shape(pic_handle* h) {
-  h->G = h->sm_count * h->blocks_per_sm;
-  h->mcc_blocks = h->sm_count;
-  h->st.G = h->G;
-  const size_t need = (size_t)h->n_seg * h->G;
-  if (need > h->dcount_ints) {
-    void* p = dev_alloc(h, need * sizeof(int32_t));
-    if (!p) return PIC_ENOMEM;
-    h->st.dcount = (int32_t*)p;
-    h->dcount_ints = need;
-  }
-  h->push_smem = (size_t)h->max_nodes * 12 + 8 + (size_t)(h->n_seg + 1) * 8;
-  h->post_smem = (size_t)h->max_nodes * 8 + (size_t)kEvCap * 8 + (size_t)(h->G + 1) * 4;
+  h->push_smem = (size_t)h->max_nodes * 16 + 8 + (size_t)(h->n_seg + 1) * 8;
   h->field_smem = (size_t)h->max_nodes * 8;
   cudaError_t e = cudaFuncSetAttribute(k_push, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)h->push_smem);
@@ -242,12 +238,28 @@ int set_launch_shape(pic_handle* h) {
     e = cudaFuncSetAttribute(k_deposit, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)h->push_smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_post, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->post_smem);
-  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)h->field_smem);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push, h->push_threads, h->push_smem);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  if (occ < 1) occ = 1;
+  const int per_sm = h->blocks_per_sm > 0 ? std::min(h->blocks_per_sm, occ) : occ;
+  h->G = h->sm_count * per_sm;
+  h->st.G = h->G;
+  h->mcc_blocks = h->sm_count;
+  const size_t need = (size_t)h->n_seg * h->G;
+  if (need > h->dcount_ints) {
+    void* p = dev_alloc(h, need * sizeof(int32_t));
+    if (!p) return PIC_ENOMEM;
+    h->st.dcount = (int32_t*)p;
+    h->dcount_ints = need;
+  }
+  h->post_smem = (size_t)h->max_nodes * 32 + 8 + (size_t)kEvCap * 8 + (size_t)(h->G + 1) * 4;
+  e = cudaFuncSetAttribute(k_post, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->post_smem);
   drop_graph(h);
-  return e == cudaSuccess ? PIC_OK : PIC_ECUDA;
+  return e == cudaSuccess ? PIC_OK : cuda_fail(h, e);
 }
 
 // scratch of the counting sort: a second particle set and the histograms
@@ -284,6 +296,8 @@ void launch_sort(pic_handle* h) { sort_launch(h->st, h->sort_chunks, h->max_node
 
 cudaError_t launch_field(pic_handle* h) {
   k_deposit<<<h->G, h->push_threads, h->push_smem, h->stream>>>(h->st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   k_field<<<h->n_inst, kPostThreads, h->field_smem, h->stream>>>(h->st);
   return cudaGetLastError();
 }
@@ -291,7 +305,7 @@ cudaError_t launch_field(pic_handle* h) {
 int ensure_field(pic_handle* h) {
   if (!h->dirty) return PIC_OK;
   cudaError_t e = launch_field(h);
-  if (e != cudaSuccess) return cuda_fail(h, e);
+  if (e != cudaSuccess) return cuda_fail_at(h, e, "k_deposit/k_field launch");
   h->dirty = false;
   return PIC_OK;
 }
@@ -315,7 +329,7 @@ int build_graph(pic_handle* h, int len) {
   cudaGraph_t g = nullptr;
   const int64_t saved = h->host_step;
   cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) return cuda_fail(h, e);
+  if (e != cudaSuccess) return cuda_fail_at(h, e, "cudaStreamBeginCapture");
   for (int i = 0; i < len; ++i) {
     k_push<<<h->G, h->push_threads, h->push_smem, h->stream>>>(h->st);
     k_mcc<<<h->mcc_blocks, kMccThreads, 0, h->stream>>>(h->st);
@@ -323,12 +337,12 @@ int build_graph(pic_handle* h, int len) {
     if (sort_due(h, saved + i + 1)) launch_sort(h);
   }
   e = cudaStreamEndCapture(h->stream, &g);
-  if (e != cudaSuccess) return cuda_fail(h, e);
+  if (e != cudaSuccess) return cuda_fail_at(h, e, "cudaStreamEndCapture");
   e = cudaGraphInstantiate(&h->graph, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
     h->graph = nullptr;
-    return cuda_fail(h, e);
+    return cuda_fail_at(h, e, "cudaGraphInstantiate");
   }
   h->graph_len = len;
   return PIC_OK;
@@ -620,11 +634,12 @@ int pic_step(pic_handle* h, int64_t n_steps) {
   if (rc != PIC_OK) return rc;
   int64_t left = n_steps;
   const int len = h->graph_steps;
-  if (len > 0 && left >= len) {
-    // graphs are keyed by the sort phase: rebuild when it changes
-    const bool phase_ok = h->sort_period <= 0 || (h->host_step % h->sort_period) == 0;
-    while (left >= len && phase_ok && (h->sort_period <= 0 || len % h->sort_period == 0 ||
-                                       h->sort_period <= 0)) {
+  // a captured graph bakes in where the periodic sort falls: use it only on
+  // sort-aligned starts with a sort-aligned length
+  const bool aligned = h->sort_period <= 0 ||
+                       (len % h->sort_period == 0 && h->host_step % h->sort_period == 0);
+  if (len > 0 && aligned) {
+    while (left >= len) {
       if (!h->graph || h->graph_len != len) {
         rc = build_graph(h, len);
         if (rc != PIC_OK) return rc;
@@ -637,7 +652,7 @@ int pic_step(pic_handle* h, int64_t n_steps) {
   }
   for (; left > 0; --left) {
     cudaError_t e = launch_step(h);
-    if (e != cudaSuccess) return cuda_fail(h, e);
+    if (e != cudaSuccess) return cuda_fail_at(h, e, "step kernel launch");
   }
   return h->sticky;
 }
@@ -777,7 +792,7 @@ int pic_get_field(pic_handle* h, int instance, double* phi, float* E, int64_t n_
 int pic_tune(pic_handle* h, const pic_tuning* t) {
   if (!h || !t || t->size != sizeof(pic_tuning)) return PIC_EINVAL;
   if (t->push_threads != 0) {
-    if (t->push_threads < 64 || t->push_threads > 1024 || t->push_threads % 32) return PIC_EINVAL;
+    if (t->push_threads < 64 || t->push_threads > 256 || t->push_threads % 32) return PIC_EINVAL;
     h->push_threads = t->push_threads;
   }
   if (t->push_blocks_per_sm != 0) {
@@ -802,6 +817,11 @@ int pic_sort(pic_handle* h) {
   if (e != cudaSuccess) return cuda_fail(h, e);
   h->dirty = true;
   return PIC_OK;
+}
+
+const char* pic_last_error(const pic_handle* h) {
+  if (!h) return "";
+  return h->last_error;
 }
 
 int pic_synchronize(pic_handle* h) {

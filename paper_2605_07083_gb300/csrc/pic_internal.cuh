@@ -31,6 +31,7 @@ struct InstConst {
   float qmdt[3];           // q/m dt per species
   double dz, V, kappa;     // kappa = dz e w / (2^24 eps0): potential per fixed-point unit
   double inv_dz;
+  double inv_nz;           // 1 / Nz
   // null-collision MCC
   uint32_t t_cand[3];      // candidate iff Philox word 0 < t_cand
   uint32_t key0[4];        // Philox key word 0 per stream (species 0..2, injection)

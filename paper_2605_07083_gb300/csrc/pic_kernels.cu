@@ -40,22 +40,118 @@ __device__ __forceinline__ int effective_blocks(long long Q, int grid, int threa
   return (int)(need < grid ? need : grid);
 }
 
-__device__ __forceinline__ void flush_acc(const long long* acc, int n_nodes, int64_t* dst) {
-  for (int j = threadIdx.x; j < n_nodes; j += blockDim.x) {
-    long long v = acc[j];
+// ------------------------------------------------------------------ deposit
+// Per-block charge histogram in shared memory with native 32-bit atomics.
+// For cell j it keeps the particle count and the sum of the fixed-point
+// fractions Q = Qh 2^12 + Ql split in two 12-bit halves, so no counter can
+// overflow before 2^20 particles have landed in one cell.  Node j's charge
+// is then sign * (cnt_j 2^24 - Qs_j + Qs_{j-1}), Qs = sum Q -- exactly the
+// linear-weight rule, in 64-bit integers at flush time.
+struct Hist {
+  unsigned* cnt;
+  unsigned* qh;
+  unsigned* ql;
+};
+
+__device__ __forceinline__ void hist_zero(const Hist& h, int n_cells) {
+  for (int j = threadIdx.x; j < n_cells; j += blockDim.x) {
+    h.cnt[j] = 0u;
+    h.qh[j] = 0u;
+    h.ql[j] = 0u;
+  }
+}
+
+__device__ __forceinline__ long long qsum(const Hist& h, int j) {
+  return (long long)h.qh[j] * 4096 + (long long)h.ql[j];
+}
+
+// node charge of cells j-1 and j; callers sync before and after
+__device__ __forceinline__ long long hist_node(const Hist& h, int j, int Nz) {
+  long long v = 0;
+  if (j < Nz) v += (long long)h.cnt[j] * kTwo24 - qsum(h, j);
+  if (j > 0) v += qsum(h, j - 1);
+  return v;
+}
+
+__device__ __forceinline__ void hist_flush(const Hist& h, int Nz, long long sgn, int64_t* dst) {
+  for (int j = threadIdx.x; j <= Nz; j += blockDim.x) {
+    const long long v = sgn * hist_node(h, j, Nz);
     if (v != 0) atomicAdd(reinterpret_cast<unsigned long long*>(dst + j), (unsigned long long)v);
   }
 }
 
-__device__ __forceinline__ void deposit_smem(long long* acc, float z, float inv_dz, int Nz,
-                                             long long sgn) {
+__device__ __forceinline__ void hist_add(const Hist& h, int j, int q) {
+  atomicAdd(&h.cnt[j], 1u);
+  atomicAdd(&h.qh[j], (unsigned)(q >> 12));
+  atomicAdd(&h.ql[j], (unsigned)(q & 4095));
+}
+
+__device__ __forceinline__ void hist_deposit(const Hist& h, float z, float inv_dz, int Nz) {
   int j;
   float f;
   cell_of(z, inv_dz, Nz, j, f);
-  long long q = frac_units(f);
-  atomicAdd(reinterpret_cast<unsigned long long*>(acc + j),
-            (unsigned long long)(sgn * ((long long)kTwo24 - q)));
-  atomicAdd(reinterpret_cast<unsigned long long*>(acc + j + 1), (unsigned long long)(sgn * q));
+  hist_add(h, j, (int)frac_units(f));
+}
+
+// Deposit up to 4 particles per lane (bit k of am: z[k] is deposited).
+// Called by all 32 lanes.  When the warp's cells span fewer than 4 cells the
+// lanes bin in registers and the warp adds 12 totals; otherwise one set of
+// atomics per particle.
+__device__ __forceinline__ void deposit_warp(const Hist& h, const float (&z)[4], unsigned am,
+                                             float inv_dz, int Nz) {
+  int j[4], q[4];
+  int jlo = 0x7fffffff, jhi = -1;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    j[k] = 0;
+    q[k] = 0;
+    if (am & (1u << k)) {
+      float f;
+      cell_of(z[k], inv_dz, Nz, j[k], f);
+      q[k] = (int)frac_units(f);
+      jlo = min(jlo, j[k]);
+      jhi = max(jhi, j[k]);
+    }
+  }
+  const int wlo = __reduce_min_sync(0xffffffffu, jlo);
+  const int whi = __reduce_max_sync(0xffffffffu, jhi);
+  if (whi < 0) return;                        // nothing to deposit in this warp
+  if (whi - wlo < 4) {
+    unsigned c[4] = {0u, 0u, 0u, 0u}, hh[4] = {0u, 0u, 0u, 0u}, ll[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (am & (1u << k)) {
+        const int b = j[k] - wlo;
+        const unsigned qh = (unsigned)(q[k] >> 12), ql = (unsigned)(q[k] & 4095);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          c[t] += (b == t) ? 1u : 0u;
+          hh[t] += (b == t) ? qh : 0u;
+          ll[t] += (b == t) ? ql : 0u;
+        }
+      }
+    }
+    const int lane = threadIdx.x & 31;
+    unsigned mine = 0u;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const unsigned sc = __reduce_add_sync(0xffffffffu, c[t]);
+      const unsigned sh = __reduce_add_sync(0xffffffffu, hh[t]);
+      const unsigned sl = __reduce_add_sync(0xffffffffu, ll[t]);
+      if (lane == t) mine = sc;
+      if (lane == 4 + t) mine = sh;
+      if (lane == 8 + t) mine = sl;
+    }
+    if (lane < 12 && mine != 0u) {
+      const int cell = wlo + (lane & 3);
+      unsigned* arr = lane < 4 ? h.cnt : (lane < 8 ? h.qh : h.ql);
+      atomicAdd(&arr[cell], mine);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (am & (1u << k)) hist_add(h, j[k], q[k]);
+  }
 }
 
 // ------------------------------------------------------------------ MCC
@@ -193,11 +289,11 @@ struct SegCtx {
   long long sgn;
 };
 
-// One particle: gather, leapfrog, wall test, deposit of the survivor, and
-// the null-collision candidate test.  Returns bit 0 = absorbed, bit 1 =
-// collision candidate (its collision is applied afterwards, out of line; a
-// collision changes velocities only, so the deposit of z is final here).
-__device__ __forceinline__ unsigned push_one(const SegCtx& c, const float* Es, long long* acc,
+// One particle: gather, leapfrog, wall test and the null-collision candidate
+// test.  Returns bit 0 = absorbed, bit 1 = collision candidate (its
+// collision is applied afterwards by k_mcc; it changes velocities only, so
+// the survivor's z is final here and is deposited by the caller).
+__device__ __forceinline__ unsigned push_one(const SegCtx& c, const float* Es,
                                              float& z, float& vz, uint32_t pid) {
   int j;
   float f;
@@ -207,7 +303,6 @@ __device__ __forceinline__ unsigned push_one(const SegCtx& c, const float* Es, l
   vz = fmaf(c.qmdt, Ez, vz);
   z = fmaf(vz, c.dt, z);
   if (!(z >= 0.0f && z < c.Lf)) return 1u;
-  deposit_smem(acc, z, c.inv_dz, c.Nz, c.sgn);
   if (c.tc != 0u) {
     const uint4 r = philox10(make_uint4(pid, c.stepw, 0u, TAG_MCC), c.k0, c.k1);
     if (r.x < c.tc) return 2u;
@@ -215,13 +310,18 @@ __device__ __forceinline__ unsigned push_one(const SegCtx& c, const float* Es, l
   return 0u;
 }
 
+constexpr int kFlushQuota = 1 << 20;      // particles per cell-counter lifetime
+
 template <bool kDepositOnly>
 __device__ __forceinline__ void push_body(const DevState& st) {
   extern __shared__ __align__(16) unsigned char smem[];
-  long long* acc = reinterpret_cast<long long*>(smem);
-  float* Es = reinterpret_cast<float*>(smem + (size_t)st.max_nodes * 8);
-  long long* segS = reinterpret_cast<long long*>(smem + (size_t)st.max_nodes * 12 +
-                                                 ((st.max_nodes & 1) ? 4 : 0));
+  const int mn = st.max_nodes;
+  float* Es = reinterpret_cast<float*>(smem);
+  Hist hist;
+  hist.cnt = reinterpret_cast<unsigned*>(smem) + mn;
+  hist.qh = hist.cnt + mn;
+  hist.ql = hist.qh + mn;
+  long long* segS = reinterpret_cast<long long*>(smem + (size_t)mn * 16 + ((mn & 1) ? 8 : 0));
   __shared__ long long ws64[32];
   __shared__ int ws32[32];
   __shared__ InstConst icS;
@@ -250,11 +350,8 @@ __device__ __forceinline__ void push_body(const DevState& st) {
     const long long s0 = segS[g], s1 = segS[g + 1];
     if (s1 <= lo || s1 == s0) continue;
     const int inst = g / 3, sp = g - 3 * inst;
+    const long long sgn = (sp == 2) ? 1LL : -1LL;
     if (inst != cur) {
-      if (cur >= 0) {
-        __syncthreads();
-        flush_acc(acc, icS.Nz + 1, st.rho_acc + icS.node_off);
-      }
       __syncthreads();
       {
         const int* src = reinterpret_cast<const int*>(st.ic + inst);
@@ -262,88 +359,94 @@ __device__ __forceinline__ void push_body(const DevState& st) {
         for (int w = threadIdx.x; w < (int)(sizeof(InstConst) / 4); w += blockDim.x) dst[w] = src[w];
       }
       __syncthreads();
-      const int nn = icS.Nz + 1;
-      for (int j = threadIdx.x; j < nn; j += blockDim.x) {
-        acc[j] = 0;
-        if (!kDepositOnly) Es[j] = st.E[icS.node_off + j];
-      }
-      __syncthreads();
+      if (!kDepositOnly)
+        for (int j = threadIdx.x; j <= icS.Nz; j += blockDim.x) Es[j] = st.E[icS.node_off + j];
       cur = inst;
     }
+    hist_zero(hist, icS.Nz);
+    __syncthreads();
     const long long q0 = (lo > s0 ? lo : s0) - s0;
     const long long q1 = (hi < s1 ? hi : s1) - s0;
     const long long off = st.seg_off[g];
     const int N = st.seg_count[g];
     float* __restrict__ zp = st.z + off;
     float* __restrict__ vzp = st.vz + off;
-    const long long sgn = (sp == 2) ? 1LL : -1LL;
-
-    if (kDepositOnly) {
-      for (long long qb = q0; qb < q1; qb += blockDim.x) {
-        const long long q = qb + threadIdx.x;
-        if (q >= q1) continue;
-        const long long i = 4 * q;
-        if (i + 3 < N) {
-          const float4 z4 = *reinterpret_cast<const float4*>(zp + i);
-          deposit_smem(acc, z4.x, icS.inv_dz_f, icS.Nz, sgn);
-          deposit_smem(acc, z4.y, icS.inv_dz_f, icS.Nz, sgn);
-          deposit_smem(acc, z4.z, icS.inv_dz_f, icS.Nz, sgn);
-          deposit_smem(acc, z4.w, icS.inv_dz_f, icS.Nz, sgn);
-        } else {
-          for (int k = 0; k < 4; ++k)
-            if (i + k < N) deposit_smem(acc, zp[i + k], icS.inv_dz_f, icS.Nz, sgn);
-        }
-      }
-      continue;
-    }
+    const uint32_t* __restrict__ idp = st.id + off;
+    const float inv_dz = icS.inv_dz_f;
+    const int Nz = icS.Nz;
+    int64_t* rdst = st.rho_acc + icS.node_off;
+    long long quota = 0;
 
     SegCtx c;
-    c.inv_dz = icS.inv_dz_f;
+    c.inv_dz = inv_dz;
     c.Lf = icS.L_f;
     c.dt = icS.dt_f;
     c.qmdt = icS.qmdt[sp];
-    c.Nz = icS.Nz;
+    c.Nz = Nz;
     c.tc = icS.t_cand[sp];
     c.k0 = icS.key0[sp];
     c.k1 = icS.key1;
-    c.step = st.dyn[inst].step;
+    c.step = kDepositOnly ? 0 : st.dyn[inst].step;
     c.stepw = (uint32_t)c.step;
     c.sgn = sgn;
-    const uint32_t* __restrict__ idp = st.id + off;
     uint32_t* dbuf = st.dead_buf + off + 4 * q0;
     int dead_run = 0;
 
     for (long long qb = q0; qb < q1; qb += blockDim.x) {
+      if (quota >= kFlushQuota - 4LL * blockDim.x) {      // counters near their limit
+        __syncthreads();
+        hist_flush(hist, Nz, sgn, rdst);
+        __syncthreads();
+        hist_zero(hist, Nz);
+        __syncthreads();
+        quota = 0;
+      }
+      quota += 4LL * blockDim.x;
       const long long q = qb + threadIdx.x;
-      unsigned dm = 0, cm = 0;
+      unsigned dm = 0, cm = 0, am = 0;
+      float zz[4] = {0.0f, 0.0f, 0.0f, 0.0f};
       if (q < q1) {
         const long long i = 4 * q;
         if (i + 3 < N) {
           float4 z4 = __ldcs(reinterpret_cast<const float4*>(zp + i));
-          float4 v4 = __ldcs(reinterpret_cast<const float4*>(vzp + i));
-          const uint4 id4 = __ldcs(reinterpret_cast<const uint4*>(idp + i));
-          const unsigned r0 = push_one(c, Es, acc, z4.x, v4.x, id4.x);
-          const unsigned r1 = push_one(c, Es, acc, z4.y, v4.y, id4.y);
-          const unsigned r2 = push_one(c, Es, acc, z4.z, v4.z, id4.z);
-          const unsigned r3 = push_one(c, Es, acc, z4.w, v4.w, id4.w);
-          dm = (r0 & 1u) | ((r1 & 1u) << 1) | ((r2 & 1u) << 2) | ((r3 & 1u) << 3);
-          cm = (r0 >> 1) | ((r1 >> 1) << 1) | ((r2 >> 1) << 2) | ((r3 >> 1) << 3);
-          __stcs(reinterpret_cast<float4*>(zp + i), z4);
-          __stcs(reinterpret_cast<float4*>(vzp + i), v4);
+          if (kDepositOnly) {
+            am = 0xFu;
+          } else {
+            float4 v4 = __ldcs(reinterpret_cast<const float4*>(vzp + i));
+            const uint4 id4 = __ldcs(reinterpret_cast<const uint4*>(idp + i));
+            const unsigned r0 = push_one(c, Es, z4.x, v4.x, id4.x);
+            const unsigned r1 = push_one(c, Es, z4.y, v4.y, id4.y);
+            const unsigned r2 = push_one(c, Es, z4.z, v4.z, id4.z);
+            const unsigned r3 = push_one(c, Es, z4.w, v4.w, id4.w);
+            dm = (r0 & 1u) | ((r1 & 1u) << 1) | ((r2 & 1u) << 2) | ((r3 & 1u) << 3);
+            cm = (r0 >> 1) | ((r1 >> 1) << 1) | ((r2 >> 1) << 2) | ((r3 >> 1) << 3);
+            am = ~dm & 0xFu;
+            __stcs(reinterpret_cast<float4*>(zp + i), z4);
+            __stcs(reinterpret_cast<float4*>(vzp + i), v4);
+          }
+          zz[0] = z4.x; zz[1] = z4.y; zz[2] = z4.z; zz[3] = z4.w;
         } else {
-          for (int k = 0; k < 4; ++k) {
-            if (i + k < N) {
-              float zz = zp[i + k], vv = vzp[i + k];
-              const uint32_t pid = idp[i + k];
-              const unsigned r = push_one(c, Es, acc, zz, vv, pid);
-              if (r & 1u) dm |= 1u << k;
-              if (r & 2u) cm |= 1u << k;
-              zp[i + k] = zz;
-              vzp[i + k] = vv;
+          for (int k2 = 0; k2 < 4; ++k2) {
+            if (i + k2 < N) {
+              float zv = zp[i + k2];
+              if (!kDepositOnly) {
+                float vv = vzp[i + k2];
+                const unsigned r = push_one(c, Es, zv, vv, idp[i + k2]);
+                if (r & 1u) dm |= 1u << k2;
+                if (r & 2u) cm |= 1u << k2;
+                zp[i + k2] = zv;
+                vzp[i + k2] = vv;
+              }
+              if (!(dm & (1u << k2))) {
+                zz[k2] = zv;
+                am |= 1u << k2;
+              }
             }
           }
         }
       }
+      deposit_warp(hist, zz, am, inv_dz, Nz);
+      if (kDepositOnly) continue;
       // null-collision candidates -> compact list (one atomic per warp)
       {
         const int cc = __popc(cm);
@@ -378,17 +481,16 @@ __device__ __forceinline__ void push_body(const DevState& st) {
         int ex = block_exclusive_scan<int>(__popc(dm), &tot, ws32);
         if (dm) {
           int w = dead_run + ex;
-          for (int k = 0; k < 4; ++k)
-            if (dm & (1u << k)) dbuf[w++] = (uint32_t)(4 * q + k);
+          for (int k2 = 0; k2 < 4; ++k2)
+            if (dm & (1u << k2)) dbuf[w++] = (uint32_t)(4 * q + k2);
         }
         dead_run += tot;
       }
     }
-    if (threadIdx.x == 0) st.dcount[(long long)g * st.G + blockIdx.x] = dead_run;
-  }
-  if (cur >= 0) {
+    if (!kDepositOnly && threadIdx.x == 0) st.dcount[(long long)g * st.G + blockIdx.x] = dead_run;
     __syncthreads();
-    flush_acc(acc, icS.Nz + 1, st.rho_acc + icS.node_off);
+    hist_flush(hist, Nz, sgn, rdst);
+    __syncthreads();
   }
 }
 
@@ -439,27 +541,21 @@ __device__ void field_solve(const InstConst& ic, long long* rho_s, float* E, dou
   for (int u = 0; u < 4; ++u)
     if (u < c && j0 + u < Nz) rho_s[j0 + u] = a[u];
   __syncthreads();
-  const double kap = ic.kappa, dz = ic.dz;
-  const double d0 = (ic.V + kap * (double)Htot) / (double)Nz;
+  // E_j = -(d_j + d_{j-1}) / (2 dz) = A + B (G_j + G_{j-1}),  A = -d0/dz, B = kappa/(2 dz)
+  const double kap = ic.kappa;
+  const double d0 = (ic.V + kap * (double)Htot) * ic.inv_nz;
+  const double A = -d0 * ic.inv_dz, B = 0.5 * kap * ic.inv_dz;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int j = j0 + u;
     if (u < c && j < Nz) {
-      const double dj = d0 - kap * (double)a[u];
-      double Ej;
-      if (j == 0) {
-        Ej = -dj / dz;
-      } else {
-        const double dm1 = d0 - kap * (double)rho_s[j - 1];
-        Ej = -(dj + dm1) / (2.0 * dz);
-      }
-      E[j] = (float)Ej;
-      phi[j] = (double)j * d0 - kap * (double)(hex + hx[u]);
+      const long long gsum = (j == 0) ? 0LL : a[u] + rho_s[j - 1];
+      E[j] = (float)fma(B, (double)gsum, A);
+      phi[j] = fma((double)j, d0, -kap * (double)(hex + hx[u]));
     }
   }
   if (threadIdx.x == 0) {
-    const double dl = d0 - kap * (double)rho_s[Nz - 1];
-    E[Nz] = (float)(-dl / dz);
+    E[Nz] = (float)fma(2.0 * B, (double)rho_s[Nz - 1], A);
     phi[Nz] = ic.V;
   }
   __syncthreads();
@@ -503,8 +599,17 @@ __device__ __forceinline__ void put_particle(const DevState& st, long long off, 
 
 __global__ void __launch_bounds__(kPostThreads) k_post(DevState st) {
   extern __shared__ __align__(16) unsigned char smem[];
+  const int mn = st.max_nodes;
   long long* rho_s = reinterpret_cast<long long*>(smem);
-  unsigned long long* evk = reinterpret_cast<unsigned long long*>(smem + (size_t)st.max_nodes * 8);
+  Hist He, Hi;                                   // appended electrons / ions
+  He.cnt = reinterpret_cast<unsigned*>(smem + (size_t)mn * 8);
+  He.qh = He.cnt + mn;
+  He.ql = He.qh + mn;
+  Hi.cnt = He.ql + mn;
+  Hi.qh = Hi.cnt + mn;
+  Hi.ql = Hi.qh + mn;
+  unsigned long long* evk =
+      reinterpret_cast<unsigned long long*>(smem + (size_t)mn * 32 + ((mn & 1) ? 8 : 0));
   int* bpre = reinterpret_cast<int*>(evk + kEvCap);
   __shared__ long long ws64[32];
   __shared__ int ws32[32];
@@ -662,7 +767,8 @@ __global__ void __launch_bounds__(kPostThreads) k_post(DevState st) {
 
   // ---- D: appends (children, emission, replenishment) and their deposit
   const int nn = ic.Nz + 1;
-  for (int j = tid; j < nn; j += nt) rho_s[j] = st.rho_acc[ic.node_off + j];
+  hist_zero(He, ic.Nz);
+  hist_zero(Hi, ic.Nz);
   __syncthreads();
   const uint32_t base_id = dyn->next_id;
   const int Nemit = sNemit;
@@ -677,11 +783,11 @@ __global__ void __launch_bounds__(kPostThreads) k_post(DevState st) {
     const long long s1 = (long long)Nn1 + k, s2 = (long long)Nn2 + k;
     if (s1 < cap1) {
       put_particle(st, off1, s1, ev.z, ev.ve[0], ev.ve[1], ev.ve[2], base_id + 2u * k);
-      deposit_smem(rho_s, ev.z, ic.inv_dz_f, ic.Nz, -1);
+      hist_deposit(He, ev.z, ic.inv_dz_f, ic.Nz);
     } else overflow = true;
     if (s2 < cap2) {
       put_particle(st, off2, s2, ev.z, ev.vi[0], ev.vi[1], ev.vi[2], base_id + 2u * k + 1u);
-      deposit_smem(rho_s, ev.z, ic.inv_dz_f, ic.Nz, 1);
+      hist_deposit(Hi, ev.z, ic.inv_dz_f, ic.Nz);
     } else overflow = true;
   }
   const uint32_t id_emit = base_id + 2u * (uint32_t)E;
@@ -694,7 +800,7 @@ __global__ void __launch_bounds__(kPostThreads) k_post(DevState st) {
     const long long s = (long long)Nn0 + k;
     if (s < cap0) {
       put_particle(st, off0, s, z, ic.sig_w * n0, ic.sig_w * n1, vz, id_emit + (uint32_t)k);
-      deposit_smem(rho_s, z, ic.inv_dz_f, ic.Nz, -1);
+      hist_deposit(He, z, ic.inv_dz_f, ic.Nz);
     } else overflow = true;
   }
   const uint32_t id_repl = id_emit + (uint32_t)Nemit;
@@ -710,19 +816,21 @@ __global__ void __launch_bounds__(kPostThreads) k_post(DevState st) {
     if (s1 < cap1) {
       put_particle(st, off1, s1, z, ic.sig_e0 * gg[0], ic.sig_e0 * gg[1], ic.sig_e0 * gg[2],
                    id_repl + 2u * k);
-      deposit_smem(rho_s, z, ic.inv_dz_f, ic.Nz, -1);
+      hist_deposit(He, z, ic.inv_dz_f, ic.Nz);
     } else overflow = true;
     if (s2 < cap2) {
       put_particle(st, off2, s2, z, ic.sig_i0 * gg[3], ic.sig_i0 * gg[4], ic.sig_i0 * gg[5],
                    id_repl + 2u * k + 1u);
-      deposit_smem(rho_s, z, ic.inv_dz_f, ic.Nz, 1);
+      hist_deposit(Hi, z, ic.inv_dz_f, ic.Nz);
     } else overflow = true;
   }
   if (__syncthreads_or(overflow) && tid == 0) atomicOr(&dyn->err, ERR_CAPACITY);
 
   // ---- E: charge of the new state and its field
   for (int j = tid; j < nn; j += nt) {
-    st.rho[ic.node_off + j] = rho_s[j];
+    const long long v = st.rho_acc[ic.node_off + j] - hist_node(He, j, ic.Nz) + hist_node(Hi, j, ic.Nz);
+    rho_s[j] = v;
+    st.rho[ic.node_off + j] = v;
     st.rho_acc[ic.node_off + j] = 0;
   }
   __syncthreads();

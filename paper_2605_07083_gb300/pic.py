@@ -104,6 +104,7 @@ ENTRY_POINTS = {
     "pic_tune": (C.c_int, [_P, C.POINTER(PicTuning)]),
     "pic_sort": (C.c_int, [_P]),
     "pic_synchronize": (C.c_int, [_P]),
+    "pic_last_error": (C.c_char_p, [_P]),
     "pic_destroy": (None, [_P]),
     "pic_strerror": (C.c_char_p, [C.c_int]),
     "pic_abi_version": (C.c_int, []),
@@ -145,9 +146,14 @@ def strerror(code: int) -> str:
         return "error %d" % code
 
 
-def _check(rc: int, what: str):
+def _check(rc: int, what: str, h=None):
     if rc != PIC_OK:
-        raise PicError(rc, what)
+        err = PicError(rc, what)
+        if h is not None and rc == PIC_ECUDA:
+            msg = load().pic_last_error(h)
+            if msg:
+                err.args = (err.args[0] + " [" + msg.decode() + "]",)
+        raise err
 
 
 def make_config(p: dict) -> PicConfig:
@@ -217,11 +223,11 @@ def pic_inject(h, instance, species, z, vx, vy, vz):
         ptrs = [a.ctypes.data for a in keep]
         n = keep[0].size
     rc = load().pic_inject(h, instance, species, n, *[C.c_void_p(p) for p in ptrs], int(on_dev))
-    _check(rc, "pic_inject")
+    _check(rc, "pic_inject", h)
 
 
 def pic_step(h, n_steps):
-    _check(load().pic_step(h, int(n_steps)), "pic_step")
+    _check(load().pic_step(h, int(n_steps)), "pic_step", h)
 
 
 def pic_profile_steps(h, n_steps) -> dict:
