@@ -107,6 +107,8 @@ def lib():
             L.oracle_events.argtypes = [P, P, C.c_int64]
             L.oracle_derived.argtypes = [P, P, P, P, P]
             L.oracle_philox4x32_10.argtypes = [P, P, P]
+            L.oracle_philox2x32_10_w0.restype = C.c_uint32
+            L.oracle_philox2x32_10_w0.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32]
             L.oracle_thomas.argtypes = [C.c_int32, C.c_double, P, P]
             L.oracle_two_body.argtypes = [C.c_double, C.c_double, P, P, C.c_double,
                                           C.c_uint32, C.c_uint32, P, P]
@@ -245,6 +247,10 @@ def philox4x32_10(ctr, key) -> np.ndarray:
     out = np.empty(4, np.uint32)
     lib().oracle_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
     return out
+
+
+def philox2x32_10_w0(c0: int, c1: int, key: int) -> int:
+    return int(lib().oracle_philox2x32_10_w0(c0, c1, key))
 
 
 def thomas(Nz: int, V: float, rhs: np.ndarray) -> np.ndarray:

@@ -65,6 +65,26 @@ Ctr philox10(Ctr c, uint32_t k0, uint32_t k1) {
     return c;
 }
 
+/* Philox2x32-10 (same paper): one 32x32->64 product per round on a 2-word
+ * counter, key bumped by the Weyl constant.  Used for the per-particle
+ * null-collision candidate word, drawn for every particle every step. */
+uint32_t philox2x32_10_w0(uint32_t c0, uint32_t c1, uint32_t k) {
+    const uint32_t M = 0xD256D193u, W = 0x9E3779B9u;
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) k += W;
+        uint64_t p = (uint64_t)M * c0;
+        uint32_t hi = (uint32_t)(p >> 32), lo = (uint32_t)p;
+        c0 = hi ^ k ^ c1;
+        c1 = lo;
+    }
+    return c0;
+}
+
+/* candidate key of a stream: seed_lo ^ stream*0x9E3779B9 ^ seed_hi */
+uint32_t cand_key(uint64_t seed, uint32_t stream) {
+    return (uint32_t)seed ^ (uint32_t)(stream * 0x9E3779B9u) ^ (uint32_t)(seed >> 32);
+}
+
 /* reading: key = (seed_lo ^ stream*0x9E3779B9, seed_hi); counter = (index,
  * step, draw block, tag).  stream = species for MCC, 3 for injection. */
 Ctr draw(uint64_t seed, uint32_t stream, uint32_t index, int64_t step,
@@ -128,6 +148,10 @@ struct oracle_sim {
 
 /* ------------------------------------------------------------------------ */
 extern "C" {
+
+uint32_t oracle_philox2x32_10_w0(uint32_t c0, uint32_t c1, uint32_t key) {
+    return philox2x32_10_w0(c0, c1, key);
+}
 
 void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
     Ctr c = {{ctr[0], ctr[1], ctr[2], ctr[3]}};
@@ -409,10 +433,12 @@ void do_step(oracle_sim* s) {
                 }
                 continue;
             }
-            /* 6: null-collision candidate test on the first word */
+            /* 6: null-collision candidate test: Philox2x32 word 0 of
+             * (id, step) under the species' candidate key */
             if (c.n_gas <= 0.0) continue;
+            uint32_t rc = philox2x32_10_w0(p.id[i], (uint32_t)n, cand_key(c.seed, (uint32_t)k));
+            if (!(rc < s->t_cand[k])) continue;
             Ctr A = draw(c.seed, (uint32_t)k, p.id[i], n, 0, TAG_MCC);
-            if (!(A.w[0] < s->t_cand[k])) continue;
             if (in_win) s->win.candidates[k] += 1;
             Ctr B = draw(c.seed, (uint32_t)k, p.id[i], n, 1, TAG_MCC);
             double nn[4];

@@ -15,7 +15,8 @@
  *   3. E^n = -dphi/dz on nodes
  *   4. gather E(z^n) + leapfrog push (only v_z is accelerated, 1D-3V)
  *   5. wall absorption z<0 (cathode) / z>=L (anode) with count + KE tallies
- *   6. null-collision MCC on survivors (Sec. 2.2, Vahedi-Surendra scheme)
+ *   6. null-collision MCC on survivors (Sec. 2.2, Vahedi-Surendra scheme):
+ *      candidate word from Philox2x32-10, collision draws from Philox4x32-10
  *   7. append ionisation children (by parent id), thermionic electrons
  *      (Sec. 2.2), replenished e-ion pairs (Sec. 2.1)
  *   8. remove absorbed particles
@@ -120,6 +121,8 @@ void    oracle_derived(const oracle_sim* s, double* nu_max, uint32_t* t_cand,
 
 /* ---- stand-alone pieces, exposed for pinning tests ---- */
 void    oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* word 0 of Philox2x32-10 of counter (c0, c1) under key */
+uint32_t oracle_philox2x32_10_w0(uint32_t c0, uint32_t c1, uint32_t key);
 /* tridiag(-1,2,-1) phi = rhs on interior nodes 1..Nz-1, phi0 = 0, phiNz = V */
 void    oracle_thomas(int32_t Nz, double V, const double* rhs, double* phi);
 /* two-body isotropic-CM elastic scattering with |g'| = gnew */

@@ -26,7 +26,7 @@ __global__ void k_count_outside(const float* z, long long n, float Lf, int* bad)
 void sort_launch(const DevState& st, int max_chunks, int max_nz, cudaStream_t s);
 size_t sort_hist_ints(const int32_t* seg_cap, const int* seg_nz, int n_seg, int64_t* hoff);
 int sort_max_chunks(const int32_t* seg_cap, int n_seg);
-cudaError_t sort_prepare(int max_nz);
+cudaError_t sort_prepare(int smem_bytes);
 }  // namespace pic
 
 using namespace pic;
@@ -187,6 +187,8 @@ InstConst derive(const pic_config& c) {
   const uint32_t slo = (uint32_t)c.seed, shi = (uint32_t)(c.seed >> 32);
   for (uint32_t s = 0; s < 4; ++s) k.key0[s] = slo ^ (uint32_t)(s * 0x9E3779B9u);
   k.key1 = shi;
+  // candidate word: Philox2x32-10 under seed_lo ^ species*0x9E3779B9 ^ seed_hi
+  for (uint32_t s = 0; s < 3; ++s) k.ckey[s] = slo ^ (uint32_t)(s * 0x9E3779B9u) ^ shi;
   // thermionic emission: N = floor(x) + [u < frac(x)], x = Gamma dt / w (Sec. 2.2)
   const double x = (c.gamma_emit * c.dt_s) / c.weight;
   const double fl = std::floor(x);
@@ -229,37 +231,53 @@ void drop_graph(pic_handle* h) {
   h->graph_len = 0;
 }
 
+// The dynamic shared-memory limit is a process-wide attribute of each kernel:
+// raise it once per device to the opt-in maximum, so that handles of
+// different grid sizes never lower it under one another's launches.
+cudaError_t raise_smem_limits(int device) {
+  static bool done[64] = {false};
+  if (device >= 0 && device < 64 && done[device]) return cudaSuccess;
+  int optin = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  if (e != cudaSuccess) return e;
+  const void* fns[] = {(const void*)k_push, (const void*)k_deposit, (const void*)k_field,
+                       (const void*)k_post};
+  for (const void* f : fns) {
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e != cudaSuccess) return e;
+  }
+  e = sort_prepare(optin);
+  if (e == cudaSuccess && device >= 0 && device < 64) done[device] = true;
+  return e;
+}
+
 int set_launch_shape(pic_handle* h) {
-  h->push_smem = (size_t)h->max_nodes * 16 + 8 + (size_t)(h->n_seg + 1) * 8;
+  h->push_smem = (size_t)h->max_nodes * 20 + 8 + (size_t)(h->n_seg + 1) * 8;
   h->field_smem = (size_t)h->max_nodes * 8;
-  cudaError_t e = cudaFuncSetAttribute(k_push, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)h->push_smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_deposit, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)h->push_smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)h->field_smem);
+  cudaError_t e = raise_smem_limits(h->device);
   if (e != cudaSuccess) return cuda_fail(h, e);
   int occ = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push, h->push_threads, h->push_smem);
   if (e != cudaSuccess) return cuda_fail(h, e);
   if (occ < 1) occ = 1;
   const int per_sm = h->blocks_per_sm > 0 ? std::min(h->blocks_per_sm, occ) : occ;
-  h->G = h->sm_count * per_sm;
+  // enough blocks that none holds more than kPushMaxParticlesPerBlock slots
+  const int64_t min_blocks = (h->total_cap + kPushMaxParticlesPerBlock - 1) / kPushMaxParticlesPerBlock;
+  h->G = (int)std::max<int64_t>((int64_t)h->sm_count * per_sm, min_blocks);
   h->st.G = h->G;
+  h->st.W = h->push_threads / 32;
   h->mcc_blocks = h->sm_count;
-  const size_t need = (size_t)h->n_seg * h->G;
+  const size_t need = (size_t)h->n_seg * h->G * (h->push_threads / 32);
   if (need > h->dcount_ints) {
     void* p = dev_alloc(h, need * sizeof(int32_t));
     if (!p) return PIC_ENOMEM;
     h->st.dcount = (int32_t*)p;
     h->dcount_ints = need;
   }
-  h->post_smem = (size_t)h->max_nodes * 32 + 8 + (size_t)kEvCap * 8 + (size_t)(h->G + 1) * 4;
-  e = cudaFuncSetAttribute(k_post, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->post_smem);
+  h->post_smem = (size_t)h->max_nodes * 32 + 8 + (size_t)kEvCap * 8 + (size_t)kDeadSmem * 4 +
+                 (size_t)(h->G * (h->push_threads / 32) + 1) * 4;
   drop_graph(h);
-  return e == cudaSuccess ? PIC_OK : cuda_fail(h, e);
+  return PIC_OK;
 }
 
 // scratch of the counting sort: a second particle set and the histograms
@@ -284,7 +302,6 @@ int sort_alloc(pic_handle* h) {
   cudaError_t e = cudaMemcpyAsync(c, hoff.data(), sizeof(int64_t) * h->n_seg, cudaMemcpyHostToDevice,
                                   h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  if (e == cudaSuccess) e = sort_prepare(h->max_nodes);
   if (e != cudaSuccess) return cuda_fail(h, e);
   h->sort_chunks = sort_max_chunks(h->seg_cap.data(), h->n_seg);
   h->sort_ready = true;
@@ -485,7 +502,7 @@ int pic_create(const pic_config* cfgs, int n_instances, void* cuda_stream,
   }
   h->total_cap = off;
   h->total_nodes = nodes;
-  if (h->total_cap > 0xFFFFFFF0LL) { pic_destroy(h); return PIC_EINVAL; }
+  if (h->total_cap > kMaxSlots) { pic_destroy(h); return PIC_EINVAL; }
 
   DevState& st = h->st;
   st.n_inst = h->n_inst;

@@ -11,6 +11,9 @@ constexpr int kMaxNz = 4096;          // shared-memory grid limit (nodes = Nz + 
 constexpr int kMaxInstances = 256;
 constexpr int kEvCap = 2048;          // ionisation events per instance per step
 constexpr int kPostThreads = 1024;
+constexpr int kPushMaxParticlesPerBlock = 1 << 20;   // cell-counter lifetime
+constexpr long long kMaxSlots = 1LL << 29;            // particle slots per handle
+constexpr int kDeadSmem = 8192;                       // absorbed slots staged in k_post
 constexpr int kTwo24 = 1 << 24;
 
 enum Tag : uint32_t { TAG_MCC = 1, TAG_EMIT = 2, TAG_EMIT_N = 3, TAG_REPL = 4 };
@@ -34,8 +37,9 @@ struct InstConst {
   double inv_nz;           // 1 / Nz
   // null-collision MCC
   uint32_t t_cand[3];      // candidate iff Philox word 0 < t_cand
-  uint32_t key0[4];        // Philox key word 0 per stream (species 0..2, injection)
+  uint32_t key0[4];        // Philox4x32 key word 0 per stream (species 0..2, injection)
   uint32_t key1;
+  uint32_t ckey[3];        // Philox2x32 candidate key per species
   float nu_max[3];
   float n_gas;
   float sig_n[3];          // neutral partner thermal speed sqrt(k T_n / M) per species
@@ -87,6 +91,7 @@ struct Event {              // one ionisation: parent id + both children
 struct DevState {
   int n_inst, n_seg;
   int G;                   // launched blocks of the particle kernels
+  int W;                   // warps per block of the particle kernels
   int max_nodes;           // max (Nz + 1) over instances
   float* z; float* vx; float* vy; float* vz; uint32_t* id;
   float* z2; float* vx2; float* vy2; float* vz2; uint32_t* id2;   // sort scratch
@@ -94,8 +99,8 @@ struct DevState {
   const int32_t* seg_cap;  // [n_seg]
   int32_t* seg_count;      // [n_seg] live particles
   int64_t* part;           // [n_seg + 2]: quad prefix of the last push, Q, G_eff
-  int32_t* dcount;         // [n_seg * G] absorbed particles per (segment, block)
-  uint32_t* dead_buf;      // [total_cap] per-block absorbed-slot lists
+  int32_t* dcount;         // [n_seg * G * W] absorbed particles per (segment, block, warp)
+  uint32_t* dead_buf;      // [total_cap] per-warp absorbed-slot lists
   uint32_t* dead_dense;    // [total_cap] ordered absorbed-slot list per segment
   Event* ev_buf;           // [n_inst * kEvCap]
   int64_t* rho_acc;        // [total_nodes] fixed-point charge being accumulated
@@ -140,6 +145,19 @@ static __device__ __noinline__ uint4 philox10_rolled(uint4 c, uint32_t k0, uint3
     k1 += 0xBB67AE85u;
   }
   return c;
+}
+
+// Philox2x32-10 word 0 (same paper): one 32x32->64 product per round on a
+// 2-word counter.  The per-particle null-collision candidate word.
+__device__ __forceinline__ uint32_t philox2x32_w0(uint32_t c0, uint32_t c1, uint32_t k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned long long p = (unsigned long long)0xD256D193u * c0;
+    c0 = (uint32_t)(p >> 32) ^ k ^ c1;
+    c1 = (uint32_t)p;
+    k += 0x9E3779B9u;
+  }
+  return c0;
 }
 
 // uniform on (0,1): (k + 1/2) 2^-23, k = r >> 9 -- exact in FP32

@@ -34,10 +34,19 @@ __device__ void seg_quad_prefix(const DevState& st, long long* segS, long long* 
   __syncthreads();
 }
 
+// blocks that get work: at least one quad per thread, and no block above
+// kPushMaxParticlesPerBlock particles (the host sizes the grid for that)
 __device__ __forceinline__ int effective_blocks(long long Q, int grid, int threads) {
   long long need = (Q + threads - 1) / threads;
+  const long long cap_need = (4 * Q + kPushMaxParticlesPerBlock - 1) / kPushMaxParticlesPerBlock;
+  if (need < cap_need) need = cap_need;
   if (need < 1) need = 1;
   return (int)(need < grid ? need : grid);
+}
+
+// quad range of warp w of a block range [q0, q1): contiguous, in warp order
+__device__ __forceinline__ long long warp_start(long long q0, long long q1, int w, int W) {
+  return q0 + ((q1 - q0) * w) / W;
 }
 
 // ------------------------------------------------------------------ deposit
@@ -161,13 +170,13 @@ __device__ __forceinline__ void deposit_warp(const Hist& h, const float (&z)[4],
 // direction.  Block 1: neutral partner velocity (Maxwellian at T_n).  Block
 // 2: ionisation energy split and the ejected electron's direction.
 // Returns the new v_z; writes v_x, v_y in place.  Rare path: kept out of line.
-__device__ __noinline__ float collide(const InstConst* __restrict__ icg, InstDyn* dyn,
+__device__ __forceinline__ float collide(const InstConst* __restrict__ icg, InstDyn* dyn,
                                       Event* evb, float* vxp, float* vyp, int sp, uint32_t pid,
                                       uint32_t stepw, long long step, float z, float vz) {
   const InstConst& ic = *icg;
   const uint32_t k0 = ic.key0[sp], k1 = ic.key1;
-  const uint4 A = philox10_rolled(make_uint4(pid, stepw, 0u, TAG_MCC), k0, k1);
-  const uint4 B = philox10_rolled(make_uint4(pid, stepw, 1u, TAG_MCC), k0, k1);
+  const uint4 A = philox10(make_uint4(pid, stepw, 0u, TAG_MCC), k0, k1);
+  const uint4 B = philox10(make_uint4(pid, stepw, 1u, TAG_MCC), k0, k1);
   float n0, n1, n2, n3;
   box_muller(B.x, B.y, n0, n1);
   box_muller(B.z, B.w, n2, n3);
@@ -206,7 +215,7 @@ __device__ __noinline__ float collide(const InstConst* __restrict__ icg, InstDyn
       nvy = fm * vy + fM * vny + fM * gn * dy;
       nvz = fm * vz + fM * vnz + fM * gn * dz;
     } else if (code == 3) {
-      const uint4 Cc = philox10_rolled(make_uint4(pid, stepw, 2u, TAG_MCC), k0, k1);
+      const uint4 Cc = philox10(make_uint4(pid, stepw, 2u, TAG_MCC), k0, k1);
       const float Eex = Erel - ic.E_iz;
       const float U = u01f(Cc.x);
       const float E1 = U * Eex, E2 = (1.0f - U) * Eex;
@@ -284,46 +293,39 @@ __global__ void __launch_bounds__(kMccThreads) k_mcc(DevState st) {
 struct SegCtx {
   float inv_dz, Lf, dt, qmdt;
   int Nz;
-  uint32_t tc, k0, k1, stepw;
-  long long step;
-  long long sgn;
+  uint32_t tc, ck, stepw;
 };
 
 // One particle: gather, leapfrog, wall test and the null-collision candidate
 // test.  Returns bit 0 = absorbed, bit 1 = collision candidate (its
 // collision is applied afterwards by k_mcc; it changes velocities only, so
 // the survivor's z is final here and is deposited by the caller).
-__device__ __forceinline__ unsigned push_one(const SegCtx& c, const float* Es,
+// Es2[j] = (E_j, E_{j+1} - E_j): one 64-bit shared load per gather
+__device__ __forceinline__ unsigned push_one(const SegCtx& c, const float2* Es2,
                                              float& z, float& vz, uint32_t pid) {
   int j;
   float f;
   cell_of(z, c.inv_dz, c.Nz, j, f);
-  const float e0 = Es[j], e1 = Es[j + 1];
-  const float Ez = fmaf(f, e1 - e0, e0);
+  const float2 e = Es2[j];
+  const float Ez = fmaf(f, e.y, e.x);
   vz = fmaf(c.qmdt, Ez, vz);
   z = fmaf(vz, c.dt, z);
   if (!(z >= 0.0f && z < c.Lf)) return 1u;
-  if (c.tc != 0u) {
-    const uint4 r = philox10(make_uint4(pid, c.stepw, 0u, TAG_MCC), c.k0, c.k1);
-    if (r.x < c.tc) return 2u;
-  }
+  if (c.tc != 0u && philox2x32_w0(pid, c.stepw, c.ck) < c.tc) return 2u;
   return 0u;
 }
-
-constexpr int kFlushQuota = 1 << 20;      // particles per cell-counter lifetime
 
 template <bool kDepositOnly>
 __device__ __forceinline__ void push_body(const DevState& st) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int mn = st.max_nodes;
-  float* Es = reinterpret_cast<float*>(smem);
+  float2* Es2 = reinterpret_cast<float2*>(smem);
   Hist hist;
-  hist.cnt = reinterpret_cast<unsigned*>(smem) + mn;
+  hist.cnt = reinterpret_cast<unsigned*>(smem + (size_t)mn * 8);
   hist.qh = hist.cnt + mn;
   hist.ql = hist.qh + mn;
-  long long* segS = reinterpret_cast<long long*>(smem + (size_t)mn * 16 + ((mn & 1) ? 8 : 0));
+  long long* segS = reinterpret_cast<long long*>(smem + (size_t)mn * 20 + ((mn & 1) ? 4 : 0));
   __shared__ long long ws64[32];
-  __shared__ int ws32[32];
   __shared__ InstConst icS;
 
   seg_quad_prefix(st, segS, ws64);
@@ -337,6 +339,7 @@ __device__ __forceinline__ void push_body(const DevState& st) {
   const long long lo = (long long)blockIdx.x * Q / Geff;
   const long long hi = ((long long)blockIdx.x + 1) * Q / Geff;
   if (lo >= hi) return;
+  const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   // first segment whose quad range ends after lo
   int glo = 0, ghi = st.n_seg - 1;
@@ -351,22 +354,28 @@ __device__ __forceinline__ void push_body(const DevState& st) {
     if (s1 <= lo || s1 == s0) continue;
     const int inst = g / 3, sp = g - 3 * inst;
     const long long sgn = (sp == 2) ? 1LL : -1LL;
+    __syncthreads();
     if (inst != cur) {
-      __syncthreads();
       {
         const int* src = reinterpret_cast<const int*>(st.ic + inst);
         int* dst = reinterpret_cast<int*>(&icS);
         for (int w = threadIdx.x; w < (int)(sizeof(InstConst) / 4); w += blockDim.x) dst[w] = src[w];
       }
       __syncthreads();
-      if (!kDepositOnly)
-        for (int j = threadIdx.x; j <= icS.Nz; j += blockDim.x) Es[j] = st.E[icS.node_off + j];
+      if (!kDepositOnly) {
+        const float* Eg = st.E + icS.node_off;
+        for (int j = threadIdx.x; j < icS.Nz; j += blockDim.x) {
+          const float e0 = Eg[j];
+          Es2[j] = make_float2(e0, Eg[j + 1] - e0);
+        }
+      }
       cur = inst;
     }
     hist_zero(hist, icS.Nz);
     __syncthreads();
     const long long q0 = (lo > s0 ? lo : s0) - s0;
     const long long q1 = (hi < s1 ? hi : s1) - s0;
+    const long long wq0 = warp_start(q0, q1, warp, W), wq1 = warp_start(q0, q1, warp + 1, W);
     const long long off = st.seg_off[g];
     const int N = st.seg_count[g];
     float* __restrict__ zp = st.z + off;
@@ -374,8 +383,6 @@ __device__ __forceinline__ void push_body(const DevState& st) {
     const uint32_t* __restrict__ idp = st.id + off;
     const float inv_dz = icS.inv_dz_f;
     const int Nz = icS.Nz;
-    int64_t* rdst = st.rho_acc + icS.node_off;
-    long long quota = 0;
 
     SegCtx c;
     c.inv_dz = inv_dz;
@@ -384,28 +391,16 @@ __device__ __forceinline__ void push_body(const DevState& st) {
     c.qmdt = icS.qmdt[sp];
     c.Nz = Nz;
     c.tc = icS.t_cand[sp];
-    c.k0 = icS.key0[sp];
-    c.k1 = icS.key1;
-    c.step = kDepositOnly ? 0 : st.dyn[inst].step;
-    c.stepw = (uint32_t)c.step;
-    c.sgn = sgn;
-    uint32_t* dbuf = st.dead_buf + off + 4 * q0;
+    c.ck = icS.ckey[sp];
+    c.stepw = kDepositOnly ? 0u : (uint32_t)st.dyn[inst].step;
+    uint32_t* dbuf = st.dead_buf + off + 4 * wq0;
     int dead_run = 0;
 
-    for (long long qb = q0; qb < q1; qb += blockDim.x) {
-      if (quota >= kFlushQuota - 4LL * blockDim.x) {      // counters near their limit
-        __syncthreads();
-        hist_flush(hist, Nz, sgn, rdst);
-        __syncthreads();
-        hist_zero(hist, Nz);
-        __syncthreads();
-        quota = 0;
-      }
-      quota += 4LL * blockDim.x;
-      const long long q = qb + threadIdx.x;
+    for (long long base = wq0; base < wq1; base += 32) {
+      const long long q = base + lane;
       unsigned dm = 0, cm = 0, am = 0;
       float zz[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-      if (q < q1) {
+      if (q < wq1) {
         const long long i = 4 * q;
         if (i + 3 < N) {
           float4 z4 = __ldcs(reinterpret_cast<const float4*>(zp + i));
@@ -414,10 +409,10 @@ __device__ __forceinline__ void push_body(const DevState& st) {
           } else {
             float4 v4 = __ldcs(reinterpret_cast<const float4*>(vzp + i));
             const uint4 id4 = __ldcs(reinterpret_cast<const uint4*>(idp + i));
-            const unsigned r0 = push_one(c, Es, z4.x, v4.x, id4.x);
-            const unsigned r1 = push_one(c, Es, z4.y, v4.y, id4.y);
-            const unsigned r2 = push_one(c, Es, z4.z, v4.z, id4.z);
-            const unsigned r3 = push_one(c, Es, z4.w, v4.w, id4.w);
+            const unsigned r0 = push_one(c, Es2, z4.x, v4.x, id4.x);
+            const unsigned r1 = push_one(c, Es2, z4.y, v4.y, id4.y);
+            const unsigned r2 = push_one(c, Es2, z4.z, v4.z, id4.z);
+            const unsigned r3 = push_one(c, Es2, z4.w, v4.w, id4.w);
             dm = (r0 & 1u) | ((r1 & 1u) << 1) | ((r2 & 1u) << 2) | ((r3 & 1u) << 3);
             cm = (r0 >> 1) | ((r1 >> 1) << 1) | ((r2 >> 1) << 2) | ((r3 >> 1) << 3);
             am = ~dm & 0xFu;
@@ -431,7 +426,7 @@ __device__ __forceinline__ void push_body(const DevState& st) {
               float zv = zp[i + k2];
               if (!kDepositOnly) {
                 float vv = vzp[i + k2];
-                const unsigned r = push_one(c, Es, zv, vv, idp[i + k2]);
+                const unsigned r = push_one(c, Es2, zv, vv, idp[i + k2]);
                 if (r & 1u) dm |= 1u << k2;
                 if (r & 2u) cm |= 1u << k2;
                 zp[i + k2] = zv;
@@ -447,54 +442,48 @@ __device__ __forceinline__ void push_body(const DevState& st) {
       }
       deposit_warp(hist, zz, am, inv_dz, Nz);
       if (kDepositOnly) continue;
-      // null-collision candidates -> compact list (one atomic per warp)
-      {
-        const int cc = __popc(cm);
-        const unsigned any = __ballot_sync(0xffffffffu, cc != 0);
-        if (any) {
-          const int lane = threadIdx.x & 31;
-          int incl = cc;
+      // collision candidates -> compact list; absorbed slots -> this warp's
+      // ordered list (warp scans, one atomic per warp with candidates)
+      const int cc = __popc(cm), dc = __popc(dm);
+      int ci = cc, di = dc;
 #pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-          }
-          const int wtot = __shfl_sync(0xffffffffu, incl, 31);
-          const int leader = __ffs(any) - 1;
-          unsigned base = 0;
-          if (lane == leader) base = atomicAdd(st.cand_count, (unsigned)wtot);
-          base = __shfl_sync(0xffffffffu, base, leader);
-          unsigned w = base + (unsigned)(incl - cc);
-          for (int k2 = 0; k2 < 4; ++k2) {
-            if (cm & (1u << k2)) {
-              if (w < (unsigned)st.cand_cap)
-                st.cand_buf[w] = ((unsigned long long)g << 32) | (unsigned long long)(4 * q + k2);
-              else
-                atomicOr(&st.dyn[inst].err, ERR_CAPACITY);
-              ++w;
-            }
+      for (int o = 1; o < 32; o <<= 1) {
+        const int yc = __shfl_up_sync(0xffffffffu, ci, o);
+        const int yd = __shfl_up_sync(0xffffffffu, di, o);
+        if (lane >= o) { ci += yc; di += yd; }
+      }
+      const int ctot = __shfl_sync(0xffffffffu, ci, 31);
+      const int dtot = __shfl_sync(0xffffffffu, di, 31);
+      if (ctot) {
+        unsigned cbase = 0;
+        if (lane == 0) cbase = atomicAdd(st.cand_count, (unsigned)ctot);
+        cbase = __shfl_sync(0xffffffffu, cbase, 0);
+        unsigned w = cbase + (unsigned)(ci - cc);
+        for (int k2 = 0; k2 < 4; ++k2) {
+          if (cm & (1u << k2)) {
+            if (w < (unsigned)st.cand_cap)
+              st.cand_buf[w] = ((unsigned long long)g << 32) | (unsigned long long)(4 * q + k2);
+            else
+              atomicOr(&st.dyn[inst].err, ERR_CAPACITY);
+            ++w;
           }
         }
       }
-      if (__syncthreads_or(dm != 0)) {
-        int tot;
-        int ex = block_exclusive_scan<int>(__popc(dm), &tot, ws32);
-        if (dm) {
-          int w = dead_run + ex;
-          for (int k2 = 0; k2 < 4; ++k2)
-            if (dm & (1u << k2)) dbuf[w++] = (uint32_t)(4 * q + k2);
-        }
-        dead_run += tot;
+      if (dtot) {
+        int w = dead_run + di - dc;
+        for (int k2 = 0; k2 < 4; ++k2)
+          if (dm & (1u << k2)) dbuf[w++] = (uint32_t)(4 * q + k2);
+        dead_run += dtot;
       }
     }
-    if (!kDepositOnly && threadIdx.x == 0) st.dcount[(long long)g * st.G + blockIdx.x] = dead_run;
+    if (!kDepositOnly && lane == 0)
+      st.dcount[((long long)g * st.G + blockIdx.x) * W + warp] = dead_run;
     __syncthreads();
-    hist_flush(hist, Nz, sgn, rdst);
-    __syncthreads();
+    hist_flush(hist, Nz, sgn, st.rho_acc + icS.node_off);
   }
 }
 
-__global__ void __launch_bounds__(256, 3) k_push(DevState st) { push_body<false>(st); }
+__global__ void __launch_bounds__(256, 4) k_push(DevState st) { push_body<false>(st); }
 __global__ void k_deposit(DevState st) { push_body<true>(st); }
 
 // ------------------------------------------------------------------ field solve
@@ -610,7 +599,8 @@ __global__ void __launch_bounds__(kPostThreads) k_post(DevState st) {
   Hi.ql = Hi.qh + mn;
   unsigned long long* evk =
       reinterpret_cast<unsigned long long*>(smem + (size_t)mn * 32 + ((mn & 1) ? 8 : 0));
-  int* bpre = reinterpret_cast<int*>(evk + kEvCap);
+  uint32_t* dd_s = reinterpret_cast<uint32_t*>(evk + kEvCap);   // kDeadSmem staged slots
+  int* bpre = reinterpret_cast<int*>(dd_s + kDeadSmem);          // [G_eff * W + 1]
   __shared__ long long ws64[32];
   __shared__ int ws32[32];
   __shared__ double wsd[32];
@@ -637,7 +627,11 @@ __global__ void __launch_bounds__(kPostThreads) k_post(DevState st) {
   const long long Q = st.part[st.n_seg];
   const int Geff = (int)st.part[st.n_seg + 1];
 
-  // ---- A: ordered absorbed lists and boundary tallies per species
+  // ---- A+B per species: ordered absorbed list, boundary tallies, then hole
+  // filling: live tail particles move, in order, into the absorbed slots
+  // below the new count
+  const int W = st.W;
+  const int npairs = Geff * W;
   for (int sp = 0; sp < 3; ++sp) {
     const int g = inst * 3 + sp;
     const long long off = st.seg_off[g];
@@ -645,34 +639,39 @@ __global__ void __launch_bounds__(kPostThreads) k_post(DevState st) {
     const long long qg = (N + 3) >> 2;
     const long long Sg = st.part[g];
     int carry = 0;
-    for (int base = 0; base < Geff; base += nt) {
-      const int b = base + tid;
+    for (int base = 0; base < npairs; base += nt) {
+      const int p = base + tid;
       int c = 0;
-      if (b < Geff && qg > 0) {
+      if (p < npairs && qg > 0) {
+        const int b = p / W, w = p - (p / W) * W;
         const long long lb = (long long)b * Q / Geff, hb = ((long long)b + 1) * Q / Geff;
-        if (lb < hb && lb < Sg + qg && hb > Sg) c = st.dcount[(long long)g * st.G + b];
+        if (lb < hb && lb < Sg + qg && hb > Sg) c = st.dcount[((long long)g * st.G + b) * W + w];
       }
       int tot;
       const int ex = block_exclusive_scan<int>(c, &tot, ws32);
-      if (b < Geff) bpre[b] = carry + ex;
+      if (p < npairs) bpre[p] = carry + ex;
       carry += tot;
     }
-    if (tid == 0) bpre[Geff] = carry;
+    if (tid == 0) bpre[npairs] = carry;
     __syncthreads();
     const int D = carry;
+    uint32_t* dd = (D <= kDeadSmem) ? dd_s : st.dead_dense + off;
     long long cnt0 = 0, cnt1 = 0;
     double ke0 = 0.0, ke1 = 0.0;
     const double mw = 0.5 * ic.m_d[sp] * ic.weight;
     for (int k = tid; k < D; k += nt) {
-      int blo = 0, bhi = Geff;
-      while (bhi - blo > 1) {
-        const int mid = (blo + bhi) >> 1;
-        if (bpre[mid] <= k) blo = mid; else bhi = mid;
+      int plo = 0, phi_ = npairs;
+      while (phi_ - plo > 1) {
+        const int mid = (plo + phi_) >> 1;
+        if (bpre[mid] <= k) plo = mid; else phi_ = mid;
       }
-      const long long lb = (long long)blo * Q / Geff;
-      const long long qstart = (lb > Sg ? lb : Sg) - Sg;
-      const uint32_t idx = st.dead_buf[off + 4 * qstart + (k - bpre[blo])];
-      st.dead_dense[off + k] = idx;
+      const int b = plo / W, w = plo - (plo / W) * W;
+      const long long lb = (long long)b * Q / Geff, hb = ((long long)b + 1) * Q / Geff;
+      const long long q0b = (lb > Sg ? lb : Sg) - Sg;
+      const long long q1b = (hb < Sg + qg ? hb : Sg + qg) - Sg;
+      const long long wq0 = warp_start(q0b, q1b, w, W);
+      const uint32_t idx = st.dead_buf[off + 4 * wq0 + (k - bpre[plo])];
+      dd[k] = idx;
       const float z = st.z[off + idx];
       const double vx = st.vx[off + idx], vy = st.vy[off + idx], vz = st.vz[off + idx];
       const double ke = mw * (vx * vx + vy * vy + vz * vz);
@@ -687,15 +686,8 @@ __global__ void __launch_bounds__(kPostThreads) k_post(DevState st) {
       sD[sp] = D; sN[sp] = N;
     }
     __syncthreads();
-  }
-
-  // ---- B: hole filling: live tail particles move, in order, into the
-  // absorbed slots below the new count
-  for (int sp = 0; sp < 3; ++sp) {
-    const int g = inst * 3 + sp;
-    const long long off = st.seg_off[g];
-    const int N = sN[sp], D = sD[sp], Nn = N - D;
-    const uint32_t* dd = st.dead_dense + off;
+    // hole filling
+    const int Nn = N - D;
     int lo = 0, hi = D;                         // h = #absorbed slots < Nn
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
@@ -706,14 +698,14 @@ __global__ void __launch_bounds__(kPostThreads) k_post(DevState st) {
     for (int base = 0; base < D; base += nt) {
       const int k = base + tid;
       int live = 0;
-      int t = Nn + k;
+      const int t = Nn + k;
       if (k < D) {
-        int a = h, b = D;
-        while (a < b) {
-          const int mid = (a + b) >> 1;
-          if ((int)dd[mid] < t) a = mid + 1; else b = mid;
+        int a2 = h, b2 = D;
+        while (a2 < b2) {
+          const int mid = (a2 + b2) >> 1;
+          if ((int)dd[mid] < t) a2 = mid + 1; else b2 = mid;
         }
-        live = !(a < D && (int)dd[a] == t);
+        live = !(a2 < D && (int)dd[a2] == t);
       }
       int tot;
       const int r = block_exclusive_scan<int>(live, &tot, ws32) + run;

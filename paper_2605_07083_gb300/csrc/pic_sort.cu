@@ -170,12 +170,12 @@ int sort_max_chunks(const int32_t* seg_cap, int n_seg) {
 
 size_t sort_scatter_smem(int max_nz) { return (size_t)kSortWarps * max_nz * sizeof(int); }
 
-cudaError_t sort_prepare(int max_nz) {
+// raise the kernels' dynamic shared-memory limit to smem_bytes
+cudaError_t sort_prepare(int smem_bytes) {
   cudaError_t e = cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sort_scatter_smem(max_nz));
+                                       smem_bytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sort_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(max_nz * sizeof(int)));
+    e = cudaFuncSetAttribute(k_sort_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   return e;
 }
 

@@ -41,6 +41,26 @@ def test_philox_uniform_and_bijective(oracle_mod):
     assert not np.array_equal(base, O.philox4x32_10([5, 7, 0, 1], key ^ np.uint32(1)))
 
 
+def test_philox2x32_uniform_and_bijective(oracle_mod):
+    O = oracle_mod
+    key = 0x2468ACE1
+    # for a fixed key the 10-round map of the 64-bit counter is a bijection:
+    # distinct counters never collide on the full output, and word 0 alone
+    # spreads uniformly
+    w = np.array([O.philox2x32_10_w0(i, 7, key) for i in range(1 << 14)], np.uint64)
+    assert np.unique(w).size > (1 << 14) - 4           # 32-bit birthday collisions only
+    hist = np.bincount((w >> np.uint64(24)).astype(np.int64), minlength=256)
+    assert stats.chisquare(hist).pvalue > 1e-4
+    # the fraction below a threshold is the threshold (the candidate test)
+    t = 1 << 30
+    frac = (w < t).mean()
+    assert abs(frac - 0.25) < 4 * math.sqrt(0.25 * 0.75 / w.size)
+    flips = [bin(O.philox2x32_10_w0(5, 7, key) ^ O.philox2x32_10_w0(5 ^ (1 << b), 7, key)).count("1")
+             for b in range(32)]
+    assert 12 <= np.mean(flips) <= 20
+    assert O.philox2x32_10_w0(5, 7, key) != O.philox2x32_10_w0(5, 8, key)
+
+
 # ---------------------------------------------------------------- Poisson
 def test_thomas_uniform_charge_is_exact_quadratic(oracle_mod):
     """-phi'' = rho/eps0 with constant rho: the 3-point Laplacian is exact for
