@@ -231,6 +231,16 @@ void drop_graph(pic_handle* h) {
   h->graph_len = 0;
 }
 
+// dynamic shared memory a kernel may request: the opt-in maximum less its
+// static shared memory
+cudaError_t set_dynamic_smem_limit(const void* f, int optin) {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, f);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              optin - (int)a.sharedSizeBytes);
+}
+
 // The dynamic shared-memory limit is a process-wide attribute of each kernel:
 // raise it once per device to the opt-in maximum, so that handles of
 // different grid sizes never lower it under one another's launches.
@@ -243,7 +253,7 @@ cudaError_t raise_smem_limits(int device) {
   const void* fns[] = {(const void*)k_push, (const void*)k_deposit, (const void*)k_field,
                        (const void*)k_post};
   for (const void* f : fns) {
-    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    e = set_dynamic_smem_limit(f, optin);
     if (e != cudaSuccess) return e;
   }
   e = sort_prepare(optin);

@@ -170,13 +170,19 @@ int sort_max_chunks(const int32_t* seg_cap, int n_seg) {
 
 size_t sort_scatter_smem(int max_nz) { return (size_t)kSortWarps * max_nz * sizeof(int); }
 
-// raise the kernels' dynamic shared-memory limit to smem_bytes
-cudaError_t sort_prepare(int smem_bytes) {
-  cudaError_t e = cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       smem_bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sort_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-  return e;
+// raise the kernels' dynamic shared-memory limit to the opt-in maximum less
+// their static shared memory
+cudaError_t sort_prepare(int optin) {
+  const void* fns[] = {(const void*)k_sort_scatter, (const void*)k_sort_hist};
+  for (const void* f : fns) {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, f);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               optin - (int)a.sharedSizeBytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 void sort_launch(const DevState& st, int max_chunks, int max_nz, cudaStream_t s) {
