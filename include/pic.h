@@ -216,6 +216,34 @@ int pic_synchronize(pic_handle* h);
  * call site and cudaGetErrorString.  Owned by the handle. */
 const char* pic_last_error(const pic_handle* h);
 
+/* Stable sort of one particle set by cell, allocating nothing.
+ *
+ * The paper has no counterpart: this is a library service for callers that
+ * may not allocate device memory -- code that runs after a fixed memory
+ * budget has been reserved (a real-time loop, an arena-managed host
+ * application, a plugin inside another framework's memory pool), where a
+ * cudaMalloc could fail, block or synchronise the device at the wrong time.
+ * The caller passes inputs and outputs; the scratch (a (cell, chunk)
+ * histogram) is a fixed 4 MiB device array inside this library that every
+ * GPU loading the library holds until the process exits.
+ *
+ * z..id: n input particles (device); z_out..id_out: n outputs (device), not
+ * aliasing the inputs.  Output = input stably sorted by the fixed-point cell
+ * rule with Nz = n_cells, L = gap_m (the same order as pic_sort).  Enqueued
+ * on cuda_stream.  Limits: n_cells * ceil(n / 8192) <= 2^20 (for example
+ * 4.19M particles over 2048 cells) and 1 <= n_cells <= 4096; beyond them it
+ * returns PIC_ECAPACITY without launching anything.  The first call on each
+ * device sets up that device (it looks up the scratch's device address and
+ * raises a kernel attribute) and should come before any stream capture.
+ * Every call shares the one scratch array and overwrites all of it that it
+ * reads: calls that overlap on the GPU (other streams, other threads) race
+ * and must be serialised by the caller.  No cudaMalloc, cudaFree or
+ * allocating library routine is called. */
+int pic_sort_by_cell_static(const float* z, const float* vx, const float* vy, const float* vz,
+                            const uint32_t* id, int64_t n, int32_t n_cells, double gap_m,
+                            float* z_out, float* vx_out, float* vy_out, float* vz_out,
+                            uint32_t* id_out, void* cuda_stream);
+
 /* Release the handle and all device state it owns.  NULL is ignored. */
 void pic_destroy(pic_handle* h);
 /* Static description of a PIC_E* code. */

@@ -109,6 +109,8 @@ ENTRY_POINTS = {
     "pic_strerror": (C.c_char_p, [C.c_int]),
     "pic_abi_version": (C.c_int, []),
     "pic_sizeof": (C.c_size_t, [C.c_int]),
+    "pic_sort_by_cell_static": (C.c_int, [_P, _P, _P, _P, _P, C.c_int64, C.c_int32, C.c_double,
+                                          _P, _P, _P, _P, _P, _P]),
 }
 
 _lock = threading.Lock()
