@@ -205,6 +205,7 @@ def run_ours(args, rank, world):
     n_per_launch = pushed_prof / max(prof["push_launches"], 1)
     achieved = ALG_BYTES_PER_PARTICLE * n_per_launch / (push_ms * 1e-3) / 1e9
     cpu = cpu_baseline(p, state) if not args.no_cpu else None
+    batched = run_batched() if not args.no_batched else None
     launches = 3 * args.steps
     out = {
         "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
@@ -227,11 +228,76 @@ def run_ours(args, rank, world):
                 "steps": n_e2e_steps, "includes": "pic_inject from pinned host + pic_step + "
                                                    "pic_diagnostics"},
         "gpu_launches": launches,
+        "batched_sweep": batched,
         "clocks": ck,
         "diag": {"n_live": diag["n_live"], "backflow_ratio": diag["backflow_ratio"],
                  "candidates": diag["candidates"].tolist()},
     }
     return out
+
+
+def batched_workload(n_instances=64, seed=1000, steps=100):
+    """The uneven 64-diode sweep, each diode preloaded with its target
+    in-flight emitted population (uniform positions, T_w velocities)."""
+    ps = W.batched_sweep(n_instances=n_instances, seed=seed, n_steps=steps)
+    states = []
+    for i, p in enumerate(ps):
+        n = int(p["target_in_flight"])
+        rng = np.random.default_rng(seed + 7919 * (i + 1))
+        em = W.emitted_fill(rng, n, p["L"], p["T_wall_K"])
+        em = (W.clamp_inside(em[0], p["L"]),) + tuple(em[1:])
+        x = p["gamma_emit"] * p["dt"] / p["weight"]
+        p["capacity"] = (int(n + 1.3 * x * (3 * steps + 400)) + 4096, 65536, 65536)
+        states.append(em)
+    return ps, states
+
+
+def run_batched(steps=100, warmup=20):
+    """Speed-up of one batched handle over the same diodes run one by one."""
+    import torch
+    from paper_2605_07083_gb300 import pic
+    from paper_2605_07083_gb300.autotune import autotune
+    ps, states = batched_workload(steps=steps)
+    n_tot = sum(s[0].size for s in states)
+    d = pic.Diode(ps)
+    for i, st in enumerate(states):
+        d.inject(0, *st, instance=i)
+    tuning = autotune(d, steps=10)
+    d.step(warmup)
+    d.synchronize()
+    p0 = sum(d.diagnostics(i)["particles_pushed"] for i in range(len(ps)))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(d.stream)
+    d.step(steps)
+    e1.record(d.stream)
+    e1.synchronize()
+    ms_b = e0.elapsed_time(e1)
+    pushed_b = sum(d.diagnostics(i)["particles_pushed"] for i in range(len(ps))) - p0
+    d.close()
+    del d
+    ms_seq, pushed_s = 0.0, 0
+    for p, st in zip(ps, states):
+        s1 = pic.Diode(p)
+        s1.inject(0, *st)
+        s1.step(warmup)
+        s1.synchronize()
+        q0 = s1.diagnostics()["particles_pushed"]
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s1.stream)
+        s1.step(steps)
+        b.record(s1.stream)
+        b.synchronize()
+        ms_seq += a.elapsed_time(b)
+        pushed_s += s1.diagnostics()["particles_pushed"] - q0
+        s1.close()
+    return {"instances": len(ps), "particles_initial": int(n_tot), "steps": steps,
+            "ms_per_step_batched": ms_b / steps, "ms_per_step_sequential": ms_seq / steps,
+            "speedup": ms_seq / ms_b,
+            "value_batched": pushed_b / (ms_b * 1e-3), "value_sequential": pushed_s / (ms_seq * 1e-3),
+            "unit": "particle-steps/s",
+            "tuning": {k: tuning[k] for k in ("push_threads", "push_blocks_per_sm", "sort_period")},
+            "workload": "64 He diodes: Gamma U[5,9]e19, gap U[1,5] mm (cells = gap/2.5 um), "
+                        "n_He logU[1e21,1e22], 5e4-4e6 emitted e preloaded (log-uniform), 10 V"}
 
 
 def cpu_baseline(p, state, budget_s=12.0):
@@ -306,6 +372,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-diode sweep")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

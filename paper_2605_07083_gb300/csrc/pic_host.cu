@@ -262,7 +262,8 @@ cudaError_t raise_smem_limits(int device) {
 }
 
 int set_launch_shape(pic_handle* h) {
-  h->push_smem = (size_t)h->max_nodes * 20 + 8 + (size_t)(h->n_seg + 1) * 8;
+  h->push_smem = (((size_t)h->max_nodes * 20 + 8 + (size_t)(h->n_seg + 1) * 8 + 127) & ~(size_t)127) +
+                 (size_t)(h->push_threads / 32) * 2 * (kStageBytes + 8);
   h->field_smem = (size_t)h->max_nodes * 8;
   cudaError_t e = raise_smem_limits(h->device);
   if (e != cudaSuccess) return cuda_fail(h, e);
@@ -285,7 +286,7 @@ int set_launch_shape(pic_handle* h) {
     h->dcount_ints = need;
   }
   h->post_smem = (size_t)h->max_nodes * 32 + 8 + (size_t)kEvCap * 8 + (size_t)kDeadSmem * 4 +
-                 (size_t)(h->G * (h->push_threads / 32) + 1) * 4;
+                 (size_t)(h->G + 1) * 8 + (size_t)(h->G * (h->push_threads / 32) + 1) * 4;
   drop_graph(h);
   return PIC_OK;
 }

@@ -45,8 +45,9 @@ __device__ __forceinline__ int effective_blocks(long long Q, int grid, int threa
 }
 
 // quad range of warp w of a block range [q0, q1): contiguous, in warp order
+// (a block range holds at most 2^18 quads, so 32-bit arithmetic is exact)
 __device__ __forceinline__ long long warp_start(long long q0, long long q1, int w, int W) {
-  return q0 + ((q1 - q0) * w) / W;
+  return q0 + (long long)(((unsigned)(q1 - q0) * (unsigned)w) / (unsigned)W);
 }
 
 // ------------------------------------------------------------------ deposit
@@ -325,9 +326,19 @@ __device__ __forceinline__ void push_body(const DevState& st) {
   hist.qh = hist.cnt + mn;
   hist.ql = hist.qh + mn;
   long long* segS = reinterpret_cast<long long*>(smem + (size_t)mn * 20 + ((mn & 1) ? 4 : 0));
+  // per-warp double-buffered staging of (z, v_z, id) chunks and their mbarriers
+  const size_t stage_off = ((size_t)mn * 20 + 8 + (size_t)(st.n_seg + 1) * 8 + 127) & ~(size_t)127;
+  unsigned char* stages = smem + stage_off;
+  unsigned long long* bars =
+      reinterpret_cast<unsigned long long*>(stages + (size_t)(blockDim.x >> 5) * 2 * kStageBytes);
   __shared__ long long ws64[32];
   __shared__ InstConst icS;
 
+  if (!kDepositOnly && (threadIdx.x & 31) == 0) {
+    mbar_init(&bars[2 * (threadIdx.x >> 5)], 1u);
+    mbar_init(&bars[2 * (threadIdx.x >> 5) + 1], 1u);
+    fence_mbar_init();
+  }
   seg_quad_prefix(st, segS, ws64);
   const long long Q = segS[st.n_seg];
   const int Geff = effective_blocks(Q, gridDim.x, blockDim.x);
@@ -349,6 +360,9 @@ __device__ __forceinline__ void push_body(const DevState& st) {
   }
 
   int cur = -1;
+  unsigned phase = 0u;                 // parity of this warp's two stage barriers
+  unsigned char* wstage = stages + (size_t)warp * 2 * kStageBytes;
+  unsigned long long* wbar = bars + 2 * warp;
   for (int g = glo; g < st.n_seg && segS[g] < hi; ++g) {
     const long long s0 = segS[g], s1 = segS[g + 1];
     if (s1 <= lo || s1 == s0) continue;
@@ -396,19 +410,60 @@ __device__ __forceinline__ void push_body(const DevState& st) {
     uint32_t* dbuf = st.dead_buf + off + 4 * wq0;
     int dead_run = 0;
 
-    for (long long base = wq0; base < wq1; base += 32) {
+    // chunk ch of this warp = quads [wq0 + 32 ch, +32); bulk copies run two
+    // chunks ahead of the compute
+    const int nchunks = (int)((wq1 - wq0 + 31) >> 5);
+    auto issue = [&](int ch) {
+      const int s = ch & 1;
+      const long long qc = wq0 + 32LL * ch;
+      const long long nq = (wq1 - qc) < 32 ? (wq1 - qc) : 32;
+      const uint32_t bytes = (uint32_t)nq * 16u;
+      unsigned char* b = wstage + s * kStageBytes;
+      fence_proxy_async();
+      mbar_expect_tx(&wbar[s], 3u * bytes);
+      bulk_g2s(b, zp + 4 * qc, bytes, &wbar[s]);
+      bulk_g2s(b + 512, vzp + 4 * qc, bytes, &wbar[s]);
+      bulk_g2s(b + 1024, idp + 4 * qc, bytes, &wbar[s]);
+    };
+    if (!kDepositOnly && lane == 0) {
+      if (nchunks > 0) issue(0);
+      if (nchunks > 1) issue(1);
+    }
+    int ch = 0;
+    for (long long base = wq0; base < wq1; base += 32, ++ch) {
       const long long q = base + lane;
       unsigned dm = 0, cm = 0, am = 0;
       float zz[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      float4 z4s = make_float4(0.f, 0.f, 0.f, 0.f), v4s = z4s;
+      uint4 id4s = make_uint4(0u, 0u, 0u, 0u);
+      if (!kDepositOnly) {
+        const int s = ch & 1;
+        const bool arrived = mbar_wait_bounded(&wbar[s], (phase >> s) & 1u);
+        if (!__all_sync(0xffffffffu, arrived)) {
+          // the copy never completed: flag it, drain the other stage, stop
+          if (lane == 0) atomicOr(&st.dyn[inst].err, ERR_TIMEOUT);
+          if (ch + 1 < nchunks) mbar_wait_bounded(&wbar[s ^ 1], (phase >> (s ^ 1)) & 1u);
+          break;
+        }
+        phase ^= 1u << s;
+        const unsigned char* b = wstage + s * kStageBytes;
+        if (q < wq1) {
+          z4s = reinterpret_cast<const float4*>(b)[lane];
+          v4s = reinterpret_cast<const float4*>(b + 512)[lane];
+          id4s = reinterpret_cast<const uint4*>(b + 1024)[lane];
+        }
+        __syncwarp();
+        if (lane == 0 && ch + 2 < nchunks) issue(ch + 2);
+      }
       if (q < wq1) {
         const long long i = 4 * q;
         if (i + 3 < N) {
-          float4 z4 = __ldcs(reinterpret_cast<const float4*>(zp + i));
+          float4 z4 = kDepositOnly ? __ldcs(reinterpret_cast<const float4*>(zp + i)) : z4s;
           if (kDepositOnly) {
             am = 0xFu;
           } else {
-            float4 v4 = __ldcs(reinterpret_cast<const float4*>(vzp + i));
-            const uint4 id4 = __ldcs(reinterpret_cast<const uint4*>(idp + i));
+            float4 v4 = v4s;
+            const uint4 id4 = id4s;
             const unsigned r0 = push_one(c, Es2, z4.x, v4.x, id4.x);
             const unsigned r1 = push_one(c, Es2, z4.y, v4.y, id4.y);
             const unsigned r2 = push_one(c, Es2, z4.z, v4.z, id4.z);
@@ -421,12 +476,15 @@ __device__ __forceinline__ void push_body(const DevState& st) {
           }
           zz[0] = z4.x; zz[1] = z4.y; zz[2] = z4.z; zz[3] = z4.w;
         } else {
+          const float zq[4] = {z4s.x, z4s.y, z4s.z, z4s.w};
+          const float vq[4] = {v4s.x, v4s.y, v4s.z, v4s.w};
+          const uint32_t iq[4] = {id4s.x, id4s.y, id4s.z, id4s.w};
           for (int k2 = 0; k2 < 4; ++k2) {
             if (i + k2 < N) {
-              float zv = zp[i + k2];
+              float zv = kDepositOnly ? zp[i + k2] : zq[k2];
               if (!kDepositOnly) {
-                float vv = vzp[i + k2];
-                const unsigned r = push_one(c, Es2, zv, vv, idp[i + k2]);
+                float vv = vq[k2];
+                const unsigned r = push_one(c, Es2, zv, vv, iq[k2]);
                 if (r & 1u) dm |= 1u << k2;
                 if (r & 2u) cm |= 1u << k2;
                 zp[i + k2] = zv;
@@ -443,7 +501,9 @@ __device__ __forceinline__ void push_body(const DevState& st) {
       deposit_warp(hist, zz, am, inv_dz, Nz);
       if (kDepositOnly) continue;
       // collision candidates -> compact list; absorbed slots -> this warp's
-      // ordered list (warp scans, one atomic per warp with candidates)
+      // ordered list (warp scans, one atomic per warp with candidates); most
+      // iterations have neither
+      if (!__any_sync(0xffffffffu, (cm | dm) != 0u)) continue;
       const int cc = __popc(cm), dc = __popc(dm);
       int ci = cc, di = dc;
 #pragma unroll
@@ -600,7 +660,8 @@ __global__ void __launch_bounds__(kPostThreads) k_post(DevState st) {
   unsigned long long* evk =
       reinterpret_cast<unsigned long long*>(smem + (size_t)mn * 32 + ((mn & 1) ? 8 : 0));
   uint32_t* dd_s = reinterpret_cast<uint32_t*>(evk + kEvCap);   // kDeadSmem staged slots
-  int* bpre = reinterpret_cast<int*>(dd_s + kDeadSmem);          // [G_eff * W + 1]
+  long long* blo = reinterpret_cast<long long*>(dd_s + kDeadSmem);  // [G + 1] block starts
+  int* bpre = reinterpret_cast<int*>(blo + st.G + 1);               // [G_eff * W + 1]
   __shared__ long long ws64[32];
   __shared__ int ws32[32];
   __shared__ double wsd[32];
@@ -632,6 +693,8 @@ __global__ void __launch_bounds__(kPostThreads) k_post(DevState st) {
   // below the new count
   const int W = st.W;
   const int npairs = Geff * W;
+  for (int b = tid; b <= Geff; b += nt) blo[b] = (long long)b * Q / Geff;
+  __syncthreads();
   for (int sp = 0; sp < 3; ++sp) {
     const int g = inst * 3 + sp;
     const long long off = st.seg_off[g];
@@ -643,8 +706,8 @@ __global__ void __launch_bounds__(kPostThreads) k_post(DevState st) {
       const int p = base + tid;
       int c = 0;
       if (p < npairs && qg > 0) {
-        const int b = p / W, w = p - (p / W) * W;
-        const long long lb = (long long)b * Q / Geff, hb = ((long long)b + 1) * Q / Geff;
+        const int b = p / W, w = p - b * W;
+        const long long lb = blo[b], hb = blo[b + 1];
         if (lb < hb && lb < Sg + qg && hb > Sg) c = st.dcount[((long long)g * st.G + b) * W + w];
       }
       int tot;
@@ -665,8 +728,8 @@ __global__ void __launch_bounds__(kPostThreads) k_post(DevState st) {
         const int mid = (plo + phi_) >> 1;
         if (bpre[mid] <= k) plo = mid; else phi_ = mid;
       }
-      const int b = plo / W, w = plo - (plo / W) * W;
-      const long long lb = (long long)b * Q / Geff, hb = ((long long)b + 1) * Q / Geff;
+      const int b = plo / W, w = plo - b * W;
+      const long long lb = blo[b], hb = blo[b + 1];
       const long long q0b = (lb > Sg ? lb : Sg) - Sg;
       const long long q1b = (hb < Sg + qg ? hb : Sg + qg) - Sg;
       const long long wq0 = warp_start(q0b, q1b, w, W);
@@ -783,17 +846,28 @@ __global__ void __launch_bounds__(kPostThreads) k_post(DevState st) {
     } else overflow = true;
   }
   const uint32_t id_emit = base_id + 2u * (uint32_t)E;
-  for (int k = tid; k < Nemit; k += nt) {
-    const uint4 r = philox10(make_uint4((uint32_t)k, (uint32_t)step, 0u, TAG_EMIT), ic.key0[kStreamInject], ic.key1);
-    float n0, n1;
-    box_muller(r.x, r.y, n0, n1);
-    const float vz = ic.sig_w * sqrtf(-2.0f * logf(u01f(r.z)));
-    const float z = vz * ic.dt_f;
-    const long long s = (long long)Nn0 + k;
-    if (s < cap0) {
-      put_particle(st, off0, s, z, ic.sig_w * n0, ic.sig_w * n1, vz, id_emit + (uint32_t)k);
-      hist_deposit(He, z, ic.inv_dz_f, ic.Nz);
-    } else overflow = true;
+  // emitted electrons all start in the first cell: warp-aggregated deposit
+  for (int base = 0; base < Nemit; base += nt) {
+    const int k = base + tid;
+    float zz[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    unsigned am = 0u;
+    if (k < Nemit) {
+      const uint4 r = philox10(make_uint4((uint32_t)k, (uint32_t)step, 0u, TAG_EMIT),
+                               ic.key0[kStreamInject], ic.key1);
+      float n0, n1;
+      box_muller(r.x, r.y, n0, n1);
+      const float vz = ic.sig_w * sqrtf(-2.0f * logf(u01f(r.z)));
+      const float z = vz * ic.dt_f;
+      const long long s = (long long)Nn0 + k;
+      if (s < cap0) {
+        put_particle(st, off0, s, z, ic.sig_w * n0, ic.sig_w * n1, vz, id_emit + (uint32_t)k);
+        zz[0] = z;
+        am = 1u;
+      } else {
+        overflow = true;
+      }
+    }
+    deposit_warp(He, zz, am, ic.inv_dz_f, ic.Nz);
   }
   const uint32_t id_repl = id_emit + (uint32_t)Nemit;
   for (int k = tid; k < P; k += nt) {
