@@ -109,6 +109,28 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------------------ ranks
+def reduce_over_ranks(ms, pushed, e2e_s, e2e_ps, device="cpu"):
+    """Whole-job numbers of independent replicas: the slowest rank's times and
+    the sum of the particle-steps of all ranks (no collective in the data path;
+    this is the only exchange, after the timed region)."""
+    import torch
+    vals = torch.tensor([ms, float(pushed), e2e_s, float(e2e_ps)], dtype=torch.float64,
+                        device=device)
+    try:
+        import torch.distributed as td
+        dist = td.is_available() and td.is_initialized() and td.get_world_size() > 1
+    except Exception:
+        dist = False
+    if not dist:
+        return ms, float(pushed), e2e_s, float(e2e_ps)
+    mx = vals.clone()
+    td.all_reduce(mx, op=td.ReduceOp.MAX)
+    sm = vals.clone()
+    td.all_reduce(sm, op=td.ReduceOp.SUM)
+    return mx[0].item(), sm[1].item(), mx[2].item(), sm[3].item()
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank, world):
     import torch
@@ -188,15 +210,8 @@ def run_ours(args, rank, world):
     n_e2e_steps = args.warmup + args.steps
 
     # --- reduce over ranks
-    vals = torch.tensor([ms, float(pushed), e2e_s, float(e2e_ps)], dtype=torch.float64, device="cuda")
-    if dist:
-        mx = vals.clone()
-        td.all_reduce(mx, op=td.ReduceOp.MAX)
-        sm = vals.clone()
-        td.all_reduce(sm, op=td.ReduceOp.SUM)
-        ms_max, pushed_tot, e2e_max, e2e_tot = mx[0].item(), sm[1].item(), mx[2].item(), sm[3].item()
-    else:
-        ms_max, pushed_tot, e2e_max, e2e_tot = ms, float(pushed), e2e_s, float(e2e_ps)
+    ms_max, pushed_tot, e2e_max, e2e_tot = reduce_over_ranks(ms, pushed, e2e_s, e2e_ps,
+                                                             device="cuda")
     if rank != 0:
         return None
     value = pushed_tot / (ms_max * 1e-3)

@@ -244,6 +244,40 @@ int pic_sort_by_cell_static(const float* z, const float* vx, const float* vy, co
                             float* z_out, float* vx_out, float* vy_out, float* vz_out,
                             uint32_t* id_out, void* cuda_stream);
 
+/* ---- surrogate MLP (learned extension) -------------------------------
+ * 5 -> 128 -> 128 -> 128 -> 4 multilayer perceptron with exact-erf GELU on
+ * the hidden layers and a linear output, mapping normalised diode settings
+ * (emission flux, wall temperature, neutral density, gap, bias) to the
+ * Sec. 2.3 / Eq. 4 diagnostics (backflow ratio, net transport efficiency,
+ * collection efficiency, cathode energy metric).  The paper has no such
+ * model; it places the PIC runs of a flux scan.  Parameters are one flat
+ * FP32 master vector of PIC_MLP_PARAMS entries: for each layer W (n_out x
+ * n_in, row-major) then b (n_out); the forward/backward read a bfloat16 copy
+ * of it (same indices) for the weights and the FP32 biases, with FP32
+ * activations and accumulation.  All pointers are device memory; work is
+ * enqueued on cuda_stream; results are deterministic. */
+#define PIC_MLP_PARAMS 34308
+
+/* Scratch bytes pic_mlp_grad / pic_mlp_train_step need for a batch. */
+size_t pic_mlp_scratch_bytes(int64_t batch);
+/* w_bf16[p] = bfloat16(master[p]), round to nearest even. */
+int pic_mlp_cast_bf16(const float* master, uint16_t* w_bf16, void* cuda_stream);
+/* y[batch x 4] = MLP(x[batch x 5]). */
+int pic_mlp_forward(const float* master, const uint16_t* w_bf16, const float* x, int64_t batch,
+                    float* y, void* cuda_stream);
+/* Mean squared error over the batch and the 4 outputs against t[batch x 4]
+ * (*loss, device) and its gradient w.r.t. the parameters (grad[PIC_MLP_PARAMS]). */
+int pic_mlp_grad(const float* master, const uint16_t* w_bf16, const float* x, const float* t,
+                 int64_t batch, float* grad, float* loss, float* scratch, size_t scratch_bytes,
+                 void* cuda_stream);
+/* One Adam step (Kingma & Ba) at step >= 1 on the master, moments adam_m,
+ * adam_v, refreshing w_bf16; *loss (device, may be NULL) gets the batch MSE
+ * before the update. */
+int pic_mlp_train_step(float* master, uint16_t* w_bf16, float* adam_m, float* adam_v,
+                       int64_t step, float lr, float beta1, float beta2, float eps,
+                       const float* x, const float* t, int64_t batch, float* loss, float* scratch,
+                       size_t scratch_bytes, void* cuda_stream);
+
 /* Release the handle and all device state it owns.  NULL is ignored. */
 void pic_destroy(pic_handle* h);
 /* Static description of a PIC_E* code. */

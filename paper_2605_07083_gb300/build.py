@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpic.so")
-SOURCES = ["pic_kernels.cu", "pic_host.cu", "pic_sort.cu", "pic_sort_static.cu"]
+SOURCES = ["pic_kernels.cu", "pic_host.cu", "pic_sort.cu", "pic_sort_static.cu", "pic_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

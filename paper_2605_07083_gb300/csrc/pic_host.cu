@@ -278,15 +278,18 @@ int set_launch_shape(pic_handle* h) {
   h->st.G = h->G;
   h->st.W = h->push_threads / 32;
   h->mcc_blocks = h->sm_count;
-  const size_t need = (size_t)h->n_seg * h->G * (h->push_threads / 32);
+  const size_t need = (size_t)h->n_seg * h->G;
   if (need > h->dcount_ints) {
     void* p = dev_alloc(h, need * sizeof(int32_t));
     if (!p) return PIC_ENOMEM;
     h->st.dcount = (int32_t*)p;
     h->dcount_ints = need;
   }
-  h->post_smem = (size_t)h->max_nodes * 32 + 8 + (size_t)kEvCap * 8 + (size_t)kDeadSmem * 4 +
-                 (size_t)(h->G + 1) * 8 + (size_t)(h->G * (h->push_threads / 32) + 1) * 4;
+  // species phase: staged dead list + block starts + block prefix; tail:
+  // charge, two appended-particle histograms and the event keys
+  const size_t species = (size_t)kDeadSmem * 4 + (size_t)(h->G + 1) * 12 + 16;
+  const size_t tail = (size_t)h->max_nodes * 32 + 8 + (size_t)kEvCap * 8;
+  h->post_smem = std::max(species, tail);
   drop_graph(h);
   return PIC_OK;
 }
@@ -346,7 +349,7 @@ bool sort_due(const pic_handle* h, int64_t step_after) {
 cudaError_t launch_step(pic_handle* h) {
   k_push<<<h->G, h->push_threads, h->push_smem, h->stream>>>(h->st);
   k_mcc<<<h->mcc_blocks, kMccThreads, 0, h->stream>>>(h->st);
-  k_post<<<h->n_inst, kPostThreads, h->post_smem, h->stream>>>(h->st);
+  k_post<<<3 * h->n_inst, kPostThreads, h->post_smem, h->stream>>>(h->st);
   h->host_step += 1;
   if (sort_due(h, h->host_step)) launch_sort(h);
   return cudaGetLastError();
@@ -361,7 +364,7 @@ int build_graph(pic_handle* h, int len) {
   for (int i = 0; i < len; ++i) {
     k_push<<<h->G, h->push_threads, h->push_smem, h->stream>>>(h->st);
     k_mcc<<<h->mcc_blocks, kMccThreads, 0, h->stream>>>(h->st);
-    k_post<<<h->n_inst, kPostThreads, h->post_smem, h->stream>>>(h->st);
+    k_post<<<3 * h->n_inst, kPostThreads, h->post_smem, h->stream>>>(h->st);
     if (sort_due(h, saved + i + 1)) launch_sort(h);
   }
   e = cudaStreamEndCapture(h->stream, &g);
@@ -534,7 +537,8 @@ int pic_create(const pic_config* cfgs, int n_instances, void* cuda_stream,
   // candidates per step: far above the expected P_cand * N (<= 1e-2 of all slots)
   const int64_t cand_cap = std::min<int64_t>(h->total_cap / 16 + 65536, 1LL << 30);
   p[14] = dev_alloc(h, sizeof(unsigned long long) * (size_t)cand_cap + 256);
-  for (int k = 0; k < 15; ++k)
+  p[15] = dev_alloc(h, sizeof(PostScratch) * h->n_inst);
+  for (int k = 0; k < 16; ++k)
     if (!p[k]) { pic_destroy(h); return PIC_ENOMEM; }
   st.z = (float*)p[0]; st.vx = (float*)p[1]; st.vy = (float*)p[2]; st.vz = (float*)p[3];
   st.id = (uint32_t*)p[4];
@@ -554,6 +558,7 @@ int pic_create(const pic_config* cfgs, int n_instances, void* cuda_stream,
   st.cand_cap = (int)cand_cap;
   st.cand_buf = (unsigned long long*)p[14];
   st.cand_count = (unsigned int*)((char*)p[14] + sizeof(unsigned long long) * (size_t)cand_cap);
+  st.post = (PostScratch*)p[15];
   // counting-sort scratch: a second particle set plus histograms
   st.z2 = nullptr;
   cudaError_t e = cudaSuccess;
@@ -572,6 +577,7 @@ int pic_create(const pic_config* cfgs, int n_instances, void* cuda_stream,
   if (e == cudaSuccess) e = cudaMemsetAsync(st.dyn, 0, sizeof(InstDyn) * h->n_inst, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(st.part, 0, sizeof(int64_t) * (h->n_seg + 2), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(st.cand_count, 0, sizeof(unsigned int), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(st.post, 0, sizeof(PostScratch) * h->n_inst, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) { pic_destroy(h); return PIC_ECUDA; }
   int rc = set_launch_shape(h);
@@ -705,7 +711,7 @@ int pic_profile_steps(pic_handle* h, int64_t n_steps, pic_profile* out) {
     cudaEventRecord(e[1], h->stream);
     k_mcc<<<h->mcc_blocks, kMccThreads, 0, h->stream>>>(h->st);
     cudaEventRecord(e[5], h->stream);
-    k_post<<<h->n_inst, kPostThreads, h->post_smem, h->stream>>>(h->st);
+    k_post<<<3 * h->n_inst, kPostThreads, h->post_smem, h->stream>>>(h->st);
     cudaEventRecord(e[2], h->stream);
     h->host_step += 1;
     out->launches += 3;

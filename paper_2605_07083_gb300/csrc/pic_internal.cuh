@@ -8,9 +8,9 @@
 namespace pic {
 
 constexpr int kMaxNz = 4096;          // shared-memory grid limit (nodes = Nz + 1)
-constexpr int kMaxInstances = 256;
+constexpr int kMaxInstances = 1024;
 constexpr int kEvCap = 2048;          // ionisation events per instance per step
-constexpr int kPostThreads = 1024;
+constexpr int kPostThreads = 512;
 constexpr int kPushMaxParticlesPerBlock = 1 << 20;   // cell-counter lifetime
 constexpr long long kMaxSlots = 1LL << 29;            // particle slots per handle
 constexpr int kDeadSmem = 8192;                       // absorbed slots staged in k_post
@@ -80,6 +80,15 @@ struct InstDyn {
   long long pushed;          // particle-steps since creation
 };
 
+// Hand-off between the per-species blocks of the post kernel and the last
+// of them to arrive, which finishes the diode's step.
+struct PostScratch {
+  int D[3], N[3], Nn[3];
+  unsigned arrive;
+  long long cnt[3][2];
+  double ke[3][2];
+};
+
 struct Event {              // one ionisation: parent id + both children
   uint32_t parent;
   float z;
@@ -99,9 +108,9 @@ struct DevState {
   const int32_t* seg_cap;  // [n_seg]
   int32_t* seg_count;      // [n_seg] live particles
   int64_t* part;           // [n_seg + 2]: quad prefix of the last push, Q, G_eff
-  int32_t* dcount;         // [n_seg * G * W] absorbed particles per (segment, block, warp)
-  uint32_t* dead_buf;      // [total_cap] per-warp absorbed-slot lists
-  uint32_t* dead_dense;    // [total_cap] ordered absorbed-slot list per segment
+  int32_t* dcount;         // [n_seg * G] absorbed particles per (segment, block)
+  uint32_t* dead_buf;      // [total_cap] per-warp absorbed-slot lists (push), staging (post)
+  uint32_t* dead_dense;    // [total_cap] per-block ordered absorbed-slot lists
   Event* ev_buf;           // [n_inst * kEvCap]
   int64_t* rho_acc;        // [total_nodes] fixed-point charge being accumulated
   int64_t* rho;            // [total_nodes] charge of the current state
@@ -114,6 +123,7 @@ struct DevState {
   int cand_cap;
   const InstConst* ic;
   InstDyn* dyn;
+  PostScratch* post;       // [n_inst]
 };
 
 // ---------------------------------------------------------------- Philox4x32-10

@@ -332,6 +332,7 @@ __device__ __forceinline__ void push_body(const DevState& st) {
   unsigned long long* bars =
       reinterpret_cast<unsigned long long*>(stages + (size_t)(blockDim.x >> 5) * 2 * kStageBytes);
   __shared__ long long ws64[32];
+  __shared__ int wcount[32];
   __shared__ InstConst icS;
 
   if (!kDepositOnly && (threadIdx.x & 31) == 0) {
@@ -536,8 +537,19 @@ __device__ __forceinline__ void push_body(const DevState& st) {
         dead_run += dtot;
       }
     }
-    if (!kDepositOnly && lane == 0)
-      st.dcount[((long long)g * st.G + blockIdx.x) * W + warp] = dead_run;
+    // concatenate the warps' ordered lists into one list per block
+    if (!kDepositOnly) {
+      if (lane == 0) wcount[warp] = dead_run;
+      __syncthreads();
+      int start = 0, total = 0;
+      for (int w = 0; w < W; ++w) {
+        if (w < warp) start += wcount[w];
+        total += wcount[w];
+      }
+      uint32_t* dst = st.dead_dense + off + 4 * q0 + start;
+      for (int k2 = lane; k2 < dead_run; k2 += 32) dst[k2] = dbuf[k2];
+      if (threadIdx.x == 0) st.dcount[(long long)g * st.G + blockIdx.x] = total;
+    }
     __syncthreads();
     hist_flush(hist, Nz, sgn, st.rho_acc + icS.node_off);
   }
@@ -557,12 +569,12 @@ __device__ void field_solve(const InstConst& ic, long long* rho_s, float* E, dou
                             long long* ws) {
   const int Nz = ic.Nz;
   const int nt = blockDim.x;
-  const int c = (Nz + nt - 1) / nt;            // <= 4 for Nz <= 4096, nt = 1024
+  const int c = (Nz + nt - 1) / nt;            // <= 8 for Nz <= 4096, nt = 512
   const int j0 = threadIdx.x * c;
-  long long a[4];
+  long long a[8];
   long long loc = 0;
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < 8; ++u) {
     if (u < c) {
       const int j = j0 + u;
       const long long v = (j >= 1 && j < Nz) ? rho_s[j] : 0LL;
@@ -572,10 +584,10 @@ __device__ void field_solve(const InstConst& ic, long long* rho_s, float* E, dou
   }
   long long tot;
   const long long ex = block_exclusive_scan<long long>(loc, &tot, ws);
-  long long hx[4];
+  long long hx[8];
   long long lsum = 0;
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < 8; ++u) {
     if (u < c) {
       a[u] += ex;
       if (j0 + u < Nz) {
@@ -587,7 +599,7 @@ __device__ void field_solve(const InstConst& ic, long long* rho_s, float* E, dou
   long long Htot;
   const long long hex = block_exclusive_scan<long long>(lsum, &Htot, ws);
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < 8; ++u)
     if (u < c && j0 + u < Nz) rho_s[j0 + u] = a[u];
   __syncthreads();
   // E_j = -(d_j + d_{j-1}) / (2 dz) = A + B (G_j + G_{j-1}),  A = -d0/dz, B = kappa/(2 dz)
@@ -595,7 +607,7 @@ __device__ void field_solve(const InstConst& ic, long long* rho_s, float* E, dou
   const double d0 = (ic.V + kap * (double)Htot) * ic.inv_nz;
   const double A = -d0 * ic.inv_dz, B = 0.5 * kap * ic.inv_dz;
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < 8; ++u) {
     const int j = j0 + u;
     if (u < c && j < Nz) {
       const long long gsum = (j == 0) ? 0LL : a[u] + rho_s[j - 1];
@@ -646,112 +658,121 @@ __device__ __forceinline__ void put_particle(const DevState& st, long long off, 
   st.id[off + slot] = id;
 }
 
+// sum of (c0, c1, e0, e1) over the block, fixed order; valid in thread 0
+__device__ __forceinline__ void block_reduce4(long long& c0, long long& c1, double& e0, double& e1,
+                                              long long* wsl, double* wsd) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    c0 += __shfl_down_sync(0xffffffffu, c0, o);
+    c1 += __shfl_down_sync(0xffffffffu, c1, o);
+    e0 += __shfl_down_sync(0xffffffffu, e0, o);
+    e1 += __shfl_down_sync(0xffffffffu, e1, o);
+  }
+  if (lane == 0) {
+    wsl[wid] = c0;
+    wsl[32 + wid] = c1;
+    wsd[wid] = e0;
+    wsd[32 + wid] = e1;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    c0 = lane < nw ? wsl[lane] : 0LL;
+    c1 = lane < nw ? wsl[32 + lane] : 0LL;
+    e0 = lane < nw ? wsd[lane] : 0.0;
+    e1 = lane < nw ? wsd[32 + lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      c0 += __shfl_down_sync(0xffffffffu, c0, o);
+      c1 += __shfl_down_sync(0xffffffffu, c1, o);
+      e0 += __shfl_down_sync(0xffffffffu, e0, o);
+      e1 += __shfl_down_sync(0xffffffffu, e1, o);
+    }
+  }
+  __syncthreads();
+}
+
+// Three blocks per diode, one per species: ordered absorbed list, boundary
+// tallies, deterministic hole filling.  The last of the three to finish
+// (an arrival counter; nothing waits) appends the step's new particles,
+// deposits them and solves the field.
 __global__ void __launch_bounds__(kPostThreads) k_post(DevState st) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int mn = st.max_nodes;
-  long long* rho_s = reinterpret_cast<long long*>(smem);
-  Hist He, Hi;                                   // appended electrons / ions
-  He.cnt = reinterpret_cast<unsigned*>(smem + (size_t)mn * 8);
-  He.qh = He.cnt + mn;
-  He.ql = He.qh + mn;
-  Hi.cnt = He.ql + mn;
-  Hi.qh = Hi.cnt + mn;
-  Hi.ql = Hi.qh + mn;
-  unsigned long long* evk =
-      reinterpret_cast<unsigned long long*>(smem + (size_t)mn * 32 + ((mn & 1) ? 8 : 0));
-  uint32_t* dd_s = reinterpret_cast<uint32_t*>(evk + kEvCap);   // kDeadSmem staged slots
-  long long* blo = reinterpret_cast<long long*>(dd_s + kDeadSmem);  // [G + 1] block starts
-  int* bpre = reinterpret_cast<int*>(blo + st.G + 1);               // [G_eff * W + 1]
+  __shared__ long long wsl[64];
+  __shared__ double wsd2[64];
   __shared__ long long ws64[32];
   __shared__ int ws32[32];
-  __shared__ double wsd[32];
   __shared__ InstConst ic;
   __shared__ int sD[3], sN[3], sNn[3];
   __shared__ long long sCnt[3][2];
   __shared__ double sKe[3][2];
-  __shared__ int sNemit, sE;
+  __shared__ int sNemit, sE, sLast;
 
-  const int inst = blockIdx.x;
+  const int inst = blockIdx.x / 3, my_sp = blockIdx.x - 3 * inst;
   const int tid = threadIdx.x, nt = blockDim.x;
-  if (inst == 0 && tid == 0) {
-    if (*st.cand_count > (unsigned)st.cand_cap) atomicOr(&st.dyn[0].err, ERR_CAPACITY);
-    *st.cand_count = 0u;
-  }
   {
     const int* src = reinterpret_cast<const int*>(st.ic + inst);
     int* dst = reinterpret_cast<int*>(&ic);
     for (int w = tid; w < (int)(sizeof(InstConst) / 4); w += nt) dst[w] = src[w];
   }
-  __syncthreads();
   InstDyn* dyn = st.dyn + inst;
-  const long long step = dyn->step;
+  PostScratch* ps = st.post + inst;
   const long long Q = st.part[st.n_seg];
   const int Geff = (int)st.part[st.n_seg + 1];
 
-  // ---- A+B per species: ordered absorbed list, boundary tallies, then hole
-  // filling: live tail particles move, in order, into the absorbed slots
-  // below the new count
-  const int W = st.W;
-  const int npairs = Geff * W;
-  for (int b = tid; b <= Geff; b += nt) blo[b] = (long long)b * Q / Geff;
-  __syncthreads();
-  for (int sp = 0; sp < 3; ++sp) {
+  // ---- species phase
+  {
+    uint32_t* dd_s = reinterpret_cast<uint32_t*>(smem);                 // kDeadSmem slots
+    long long* blo = reinterpret_cast<long long*>(dd_s + kDeadSmem);    // [Geff + 1]
+    int* bpre = reinterpret_cast<int*>(blo + Geff + 1);                 // [Geff + 1]
+    const int sp = my_sp;
     const int g = inst * 3 + sp;
     const long long off = st.seg_off[g];
     const int N = st.seg_count[g];
     const long long qg = (N + 3) >> 2;
     const long long Sg = st.part[g];
+    for (int b = tid; b <= Geff; b += nt) blo[b] = (long long)b * Q / Geff;
+    __syncthreads();
     int carry = 0;
-    for (int base = 0; base < npairs; base += nt) {
-      const int p = base + tid;
+    for (int base = 0; base < Geff; base += nt) {
+      const int b = base + tid;
       int c = 0;
-      if (p < npairs && qg > 0) {
-        const int b = p / W, w = p - b * W;
+      if (b < Geff && qg > 0) {
         const long long lb = blo[b], hb = blo[b + 1];
-        if (lb < hb && lb < Sg + qg && hb > Sg) c = st.dcount[((long long)g * st.G + b) * W + w];
+        if (lb < hb && lb < Sg + qg && hb > Sg) c = st.dcount[(long long)g * st.G + b];
       }
       int tot;
       const int ex = block_exclusive_scan<int>(c, &tot, ws32);
-      if (p < npairs) bpre[p] = carry + ex;
+      if (b < Geff) bpre[b] = carry + ex;
       carry += tot;
     }
-    if (tid == 0) bpre[npairs] = carry;
+    if (tid == 0) bpre[Geff] = carry;
     __syncthreads();
     const int D = carry;
-    uint32_t* dd = (D <= kDeadSmem) ? dd_s : st.dead_dense + off;
+    uint32_t* dd = (D <= kDeadSmem) ? dd_s : st.dead_buf + off;
     long long cnt0 = 0, cnt1 = 0;
     double ke0 = 0.0, ke1 = 0.0;
     const double mw = 0.5 * ic.m_d[sp] * ic.weight;
     for (int k = tid; k < D; k += nt) {
-      int plo = 0, phi_ = npairs;
-      while (phi_ - plo > 1) {
-        const int mid = (plo + phi_) >> 1;
-        if (bpre[mid] <= k) plo = mid; else phi_ = mid;
+      int blo_i = 0, bhi_i = Geff;
+      while (bhi_i - blo_i > 1) {
+        const int mid = (blo_i + bhi_i) >> 1;
+        if (bpre[mid] <= k) blo_i = mid; else bhi_i = mid;
       }
-      const int b = plo / W, w = plo - b * W;
-      const long long lb = blo[b], hb = blo[b + 1];
+      const long long lb = blo[blo_i];
       const long long q0b = (lb > Sg ? lb : Sg) - Sg;
-      const long long q1b = (hb < Sg + qg ? hb : Sg + qg) - Sg;
-      const long long wq0 = warp_start(q0b, q1b, w, W);
-      const uint32_t idx = st.dead_buf[off + 4 * wq0 + (k - bpre[plo])];
+      const uint32_t idx = st.dead_dense[off + 4 * q0b + (k - bpre[blo_i])];
       dd[k] = idx;
       const float z = st.z[off + idx];
       const double vx = st.vx[off + idx], vy = st.vy[off + idx], vz = st.vz[off + idx];
       const double ke = mw * (vx * vx + vy * vy + vz * vz);
       if (z < 0.0f) { cnt0 += 1; ke0 += ke; } else { cnt1 += 1; ke1 += ke; }
     }
-    const long long c0 = block_sum<long long>(cnt0, ws64);
-    const long long c1 = block_sum<long long>(cnt1, ws64);
-    const double e0 = block_sum<double>(ke0, wsd);
-    const double e1 = block_sum<double>(ke1, wsd);
-    if (tid == 0) {
-      sCnt[sp][0] = c0; sCnt[sp][1] = c1; sKe[sp][0] = e0; sKe[sp][1] = e1;
-      sD[sp] = D; sN[sp] = N;
-    }
-    __syncthreads();
+    block_reduce4(cnt0, cnt1, ke0, ke1, wsl, wsd2);   // also orders dd writes
     // hole filling
     const int Nn = N - D;
-    int lo = 0, hi = D;                         // h = #absorbed slots < Nn
+    int lo = 0, hi = D;
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
       if ((int)dd[mid] < Nn) lo = mid + 1; else hi = mid;
@@ -775,9 +796,56 @@ __global__ void __launch_bounds__(kPostThreads) k_post(DevState st) {
       if (live) move_particle(st, off, t, dd[r]);
       run += tot;
     }
-    if (tid == 0) sNn[sp] = Nn;
+    // every thread's moves are complete and visible before the arrival: the
+    // tail appends into the slots the hole filling read from
+    __threadfence();
     __syncthreads();
+    if (tid == 0) {
+      ps->D[sp] = D;
+      ps->N[sp] = N;
+      ps->Nn[sp] = Nn;
+      ps->cnt[sp][0] = cnt0;
+      ps->cnt[sp][1] = cnt1;
+      ps->ke[sp][0] = ke0;
+      ps->ke[sp][1] = ke1;
+      __threadfence();
+      sLast = (atomicAdd(&ps->arrive, 1u) == 2u);
+    }
+    __syncthreads();
+    if (!sLast) return;
   }
+
+  // ---- tail: the last species block of this diode
+  __threadfence();
+  if (tid == 0) {
+    const volatile PostScratch* vp = ps;
+    for (int sp = 0; sp < 3; ++sp) {
+      sD[sp] = vp->D[sp];
+      sN[sp] = vp->N[sp];
+      sNn[sp] = vp->Nn[sp];
+      sCnt[sp][0] = vp->cnt[sp][0];
+      sCnt[sp][1] = vp->cnt[sp][1];
+      sKe[sp][0] = vp->ke[sp][0];
+      sKe[sp][1] = vp->ke[sp][1];
+    }
+    ps->arrive = 0u;
+    if (inst == 0) {
+      if (*st.cand_count > (unsigned)st.cand_cap) atomicOr(&dyn->err, ERR_CAPACITY);
+      *st.cand_count = 0u;
+    }
+  }
+  __syncthreads();
+  long long* rho_s = reinterpret_cast<long long*>(smem);
+  Hist He, Hi;                                   // appended electrons / ions
+  He.cnt = reinterpret_cast<unsigned*>(smem + (size_t)mn * 8);
+  He.qh = He.cnt + mn;
+  He.ql = He.qh + mn;
+  Hi.cnt = He.ql + mn;
+  Hi.qh = Hi.cnt + mn;
+  Hi.ql = Hi.qh + mn;
+  unsigned long long* evk =
+      reinterpret_cast<unsigned long long*>(smem + (size_t)mn * 32 + ((mn & 1) ? 8 : 0));
+  const long long step = dyn->step;
 
   // ---- C: ionisation events ordered by parent id
   if (tid == 0) {

@@ -111,7 +111,14 @@ ENTRY_POINTS = {
     "pic_sizeof": (C.c_size_t, [C.c_int]),
     "pic_sort_by_cell_static": (C.c_int, [_P, _P, _P, _P, _P, C.c_int64, C.c_int32, C.c_double,
                                           _P, _P, _P, _P, _P, _P]),
+    "pic_mlp_scratch_bytes": (C.c_size_t, [C.c_int64]),
+    "pic_mlp_cast_bf16": (C.c_int, [_P, _P, _P]),
+    "pic_mlp_forward": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P]),
+    "pic_mlp_grad": (C.c_int, [_P, _P, _P, _P, C.c_int64, _P, _P, _P, C.c_size_t, _P]),
+    "pic_mlp_train_step": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_float, C.c_float, C.c_float,
+                                     C.c_float, _P, _P, C.c_int64, _P, _P, C.c_size_t, _P]),
 }
+MLP_PARAMS = 34308
 
 _lock = threading.Lock()
 _lib = None

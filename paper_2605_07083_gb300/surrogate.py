@@ -1,0 +1,304 @@
+"""Learned surrogate of the diode's late-time diagnostics, and the
+surrogate-guided search for the backflow transition.
+
+The network (5 -> 128 -> 128 -> 128 -> 4, GELU) is trained and evaluated by
+the library's own kernels (pic_mlp_* in include/pic.h); PyTorch only holds
+the device buffers.  Inputs are the normalised (Gamma_emit, T_w,
+log10 n_gas, gap, bias) of a diode; outputs are its backflow ratio, net
+transport efficiency, collection efficiency (Sec. 2.3) and the cathode
+energy metric q_cooling,1 / q_emit,theory (Eq. 4 over Eq. 1).  Training data
+and every check of the network come from the batched PIC itself.
+
+The transition search locates, for each (T_w, n_gas, gap, bias) setting, the
+emission flux at which the backflow ratio crosses 1/2 inside [5, 9]e19
+m^-2 s^-1: plainly by batched bisection, or guided by the surrogate's
+predicted crossing, with PIC as judge and fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import time
+
+import numpy as np
+
+from . import pic
+from . import workloads as W
+
+TARGETS = ("backflow_ratio", "net_efficiency", "collection_efficiency", "cooling_fraction")
+
+
+def features(settings) -> np.ndarray:
+    """Inputs scaled to [-1, 1] over the surrogate ranges."""
+    X = np.empty((len(settings), len(W.SURROGATE_KEYS)), np.float32)
+    for i, s in enumerate(settings):
+        for j, k in enumerate(W.SURROGATE_KEYS):
+            lo, hi = W.SURROGATE_RANGES[k]
+            X[i, j] = 2.0 * (s[k] - lo) / (hi - lo) - 1.0
+    return X
+
+
+def targets(diag: dict) -> list:
+    q = diag["q_emit_theory"]
+    return [diag["backflow_ratio"], diag["net_efficiency"], diag["collection_efficiency"],
+            diag["q_cooling_1"] / q if q else 0.0]
+
+
+# ---------------------------------------------------------------- batched PIC
+def run_settings(settings, n_flight=2.0e4, cell_m=1.0e-5, seed0=0, max_instances=512,
+                 transits=5.0):
+    """Run every setting to its late-time window on the GPU, batched: settings
+    of similar run length share one handle.  Returns (diagnostics rows, GPU
+    milliseconds, particle-steps)."""
+    import torch
+    params = [W.setting_diode(s, n_flight=n_flight, cell_m=cell_m, seed=seed0 + i,
+                              transits=transits) for i, s in enumerate(settings)]
+    order = sorted(range(len(params)), key=lambda i: params[i]["n_steps"])
+    rows = [None] * len(params)
+    ms, psteps = 0.0, 0
+    for c0 in range(0, len(order), max_instances):
+        idx = order[c0:c0 + max_instances]
+        group = [params[i] for i in idx]
+        steps = max(p["n_steps"] for p in group)
+        d = pic.Diode(group)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(d.stream)
+        d.step(steps)
+        e1.record(d.stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        for k, i in enumerate(idx):
+            dg = d.diagnostics(k)
+            rows[i] = dg
+            psteps += dg["particles_pushed"]
+        d.close()
+    return rows, ms, psteps
+
+
+def build_dataset(n, seed, **kw):
+    settings = W.sobol_settings(n, seed)
+    rows, ms, ps = run_settings(settings, seed0=seed * 100003, **kw)
+    X = features(settings)
+    Y = np.array([targets(r) for r in rows], np.float32)
+    return settings, X, Y, {"gpu_ms": ms, "particle_steps": ps}
+
+
+# ---------------------------------------------------------------- the network
+class Surrogate:
+    """FP32 master weights + bfloat16 copy + Adam moments on the device."""
+
+    def __init__(self, seed: int = 0):
+        import torch
+        self.torch = torch
+        self.lib = pic.load()
+        rng = np.random.default_rng(seed)
+        theta = np.zeros(pic.MLP_PARAMS, np.float32)
+        p = 0
+        for i, o in zip((5, 128, 128, 128), (128, 128, 128, 4)):
+            theta[p:p + o * i] = rng.standard_normal(o * i) * math.sqrt(2.0 / i)   # He init
+            p += o * i + o
+        self.master = torch.from_numpy(theta).cuda()
+        self.w = torch.empty(pic.MLP_PARAMS, dtype=torch.int16, device="cuda")
+        self.m = torch.zeros(pic.MLP_PARAMS, device="cuda")
+        self.v = torch.zeros(pic.MLP_PARAMS, device="cuda")
+        self.step = 0
+        self._rc(self.lib.pic_mlp_cast_bf16(self._p(self.master), self._p(self.w), None), "cast")
+
+    @staticmethod
+    def _p(t):
+        return C.c_void_p(t.data_ptr())
+
+    @staticmethod
+    def _rc(rc, what):
+        if rc != 0:
+            raise pic.PicError(rc, what)
+
+    def fit(self, X, Y, steps=3000, lr=2e-3, lr_end=1e-4):
+        torch = self.torch
+        xd = torch.from_numpy(np.ascontiguousarray(X, np.float32)).cuda()
+        yd = torch.from_numpy(np.ascontiguousarray(Y, np.float32)).cuda()
+        n = X.shape[0]
+        nbytes = self.lib.pic_mlp_scratch_bytes(n)
+        scratch = torch.empty(nbytes // 4 + 1, dtype=torch.float32, device="cuda")
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        hist = []
+        for k in range(steps):
+            self.step += 1
+            a = lr_end + 0.5 * (lr - lr_end) * (1.0 + math.cos(math.pi * k / steps))
+            self._rc(self.lib.pic_mlp_train_step(
+                self._p(self.master), self._p(self.w), self._p(self.m), self._p(self.v),
+                self.step, a, 0.9, 0.999, 1e-8, self._p(xd), self._p(yd), n, self._p(loss),
+                self._p(scratch), nbytes, None), "train")
+            if k % 100 == 0 or k == steps - 1:
+                hist.append((k, loss.item()))
+        return hist
+
+    def predict(self, X) -> np.ndarray:
+        torch = self.torch
+        xd = torch.from_numpy(np.ascontiguousarray(X, np.float32)).cuda()
+        y = torch.empty((X.shape[0], 4), dtype=torch.float32, device="cuda")
+        self._rc(self.lib.pic_mlp_forward(self._p(self.master), self._p(self.w), self._p(xd),
+                                          X.shape[0], self._p(y), None), "forward")
+        torch.cuda.synchronize()
+        return y.cpu().numpy()
+
+
+# ---------------------------------------------------------------- transition search
+LO, HI, TOL = 5.0e19, 9.0e19, 0.05e19
+
+
+def _with_gamma(s, g):
+    out = dict(s)
+    out["gamma_emit"] = float(g)
+    return out
+
+
+def _eval(settings, gammas, cost, **kw):
+    rows, ms, ps = run_settings([_with_gamma(s, g) for s, g in zip(settings, gammas)], **kw)
+    cost["gpu_ms"] += ms
+    cost["particle_steps"] += ps
+    cost["runs"] += len(rows)
+    cost["rounds"] += 1
+    return np.array([r["backflow_ratio"] for r in rows])
+
+
+def _bisect(settings, a, b, open_, est, cost, **kw):
+    """Batched bisection of the crossing of 1/2 on the open settings."""
+    while open_.any():
+        idx = np.nonzero(open_)[0]
+        mid = 0.5 * (a[idx] + b[idx])
+        bf = _eval([settings[i] for i in idx], mid, cost, **kw)
+        for k, i in enumerate(idx):
+            if bf[k] >= 0.5:
+                b[i] = mid[k]
+            else:
+                a[i] = mid[k]
+            if b[i] - a[i] <= 2 * TOL:
+                est[i] = 0.5 * (a[i] + b[i])
+                open_[i] = False
+
+
+def plain_search(settings, **kw):
+    """Endpoints, then bisection to +-TOL.  est = nan: no crossing in range."""
+    n = len(settings)
+    cost = {"gpu_ms": 0.0, "particle_steps": 0, "runs": 0, "rounds": 0}
+    bf = _eval(settings + settings, [LO] * n + [HI] * n, cost, **kw)
+    a = np.full(n, LO)
+    b = np.full(n, HI)
+    est = np.full(n, np.nan)
+    open_ = (bf[:n] < 0.5) & (bf[n:] >= 0.5)
+    _bisect(settings, a, b, open_, est, cost, **kw)
+    return est, cost
+
+
+def surrogate_crossing(model, settings, n_grid=161):
+    """Predicted crossing of backflow 1/2 on a dense flux grid (nan if none)."""
+    grid = np.linspace(LO, HI, n_grid)
+    X = features([_with_gamma(s, g) for s in settings for g in grid])
+    bf = model.predict(X)[:, 0].reshape(len(settings), n_grid)
+    est = np.full(len(settings), np.nan)
+    for i in range(len(settings)):
+        up = np.nonzero((bf[i, :-1] < 0.5) & (bf[i, 1:] >= 0.5))[0]
+        if up.size:
+            k = up[0]
+            f = (0.5 - bf[i, k]) / (bf[i, k + 1] - bf[i, k])
+            est[i] = grid[k] + f * (grid[k + 1] - grid[k])
+    return est, bf, grid
+
+
+def guided_search(model, settings, max_err=0.02, **kw):
+    """PIC at the surrogate's crossing +- TOL (or at the endpoints when it
+    predicts none); accepted where PIC confirms the bracket and the surrogate
+    is within max_err of PIC there, otherwise PIC bisection takes over on the
+    bracket the evaluations leave."""
+    n = len(settings)
+    cost = {"gpu_ms": 0.0, "particle_steps": 0, "runs": 0, "rounds": 0}
+    pred, bf_grid, grid = surrogate_crossing(model, settings)
+    has = ~np.isnan(pred)
+    g_lo = np.where(has, np.clip(pred - TOL, LO, HI), LO)
+    g_hi = np.where(has, np.clip(pred + TOL, LO, HI), HI)
+    bf = _eval(settings + settings, list(g_lo) + list(g_hi), cost, **kw)
+    b_lo, b_hi = bf[:n], bf[n:]
+    s_lo = np.array([np.interp(g_lo[i], grid, bf_grid[i]) for i in range(n)])
+    s_hi = np.array([np.interp(g_hi[i], grid, bf_grid[i]) for i in range(n)])
+    err_ok = (np.abs(s_lo - b_lo) <= max_err) & (np.abs(s_hi - b_hi) <= max_err)
+    est = np.full(n, np.nan)
+    a = np.full(n, LO)
+    b = np.full(n, HI)
+    open_ = np.zeros(n, bool)
+    fallback = np.zeros(n, bool)
+    for i in range(n):
+        if b_lo[i] < 0.5 <= b_hi[i]:
+            if has[i] and err_ok[i]:
+                est[i] = 0.5 * (g_lo[i] + g_hi[i])       # bracket of width 2 TOL
+                continue
+            a[i], b[i] = g_lo[i], g_hi[i]
+            open_[i] = b[i] - a[i] > 2 * TOL
+            if not open_[i]:
+                est[i] = 0.5 * (a[i] + b[i])
+            fallback[i] = True
+        elif has[i]:
+            # the crossing is outside the predicted bracket: bisect the rest
+            fallback[i] = True
+            if b_lo[i] >= 0.5:
+                a[i], b[i] = LO, g_lo[i]
+            else:
+                a[i], b[i] = g_hi[i], HI
+            open_[i] = True
+    if fallback.any():
+        # endpoints of the remaining brackets decide whether a crossing exists
+        idx = np.nonzero(open_)[0]
+        if idx.size:
+            bfe = _eval([settings[i] for i in idx] * 2, list(a[idx]) + list(b[idx]), cost, **kw)
+            m = idx.size
+            for k, i in enumerate(idx):
+                if not (bfe[k] < 0.5 <= bfe[m + k]):
+                    open_[i] = False                      # no crossing in range
+        _bisect(settings, a, b, open_, est, cost, **kw)
+    cost["fallback"] = int(fallback.sum())
+    cost["surrogate_err_ok"] = float(err_ok[has].mean()) if has.any() else 1.0
+    return est, cost
+
+
+def run(n_train=4096, n_test=512, n_search=256, seed=4, n_flight=2.0e4, search_flight=3.0e4,
+        train_steps=3000):
+    """Whole pipeline: PIC dataset, training, held-out error, both searches."""
+    t0 = time.time()
+    _, Xtr, Ytr, c_tr = build_dataset(n_train, seed, n_flight=n_flight)
+    _, Xte, Yte, c_te = build_dataset(n_test, seed + 1, n_flight=n_flight)
+    model = Surrogate(seed)
+    hist = model.fit(Xtr, Ytr, steps=train_steps)
+    P = model.predict(Xte)
+    err = np.abs(P - Yte)
+    searches = W.random_settings(n_search, seed + 2)
+    est_p, cost_p = plain_search(searches, n_flight=search_flight)
+    est_g, cost_g = guided_search(model, searches, n_flight=search_flight)
+    both = ~np.isnan(est_p) & ~np.isnan(est_g)
+    agree = np.abs(est_p[both] - est_g[both])
+    return {
+        "dataset": {"train": n_train, "test": n_test, "train_cost": c_tr, "test_cost": c_te},
+        "training": {"steps": train_steps, "loss_first": hist[0][1], "loss_last": hist[-1][1]},
+        "held_out": {"mae": dict(zip(TARGETS, err.mean(0).tolist())),
+                     "backflow_within_0.02": float((err[:, 0] <= 0.02).mean())},
+        "search": {"settings": n_search,
+                   "plain": cost_p, "guided": cost_g,
+                   "speedup_gpu_time": cost_p["gpu_ms"] / max(cost_g["gpu_ms"], 1e-9),
+                   "speedup_particle_steps": cost_p["particle_steps"] / max(cost_g["particle_steps"], 1),
+                   "transitions_plain": int((~np.isnan(est_p)).sum()),
+                   "transitions_guided": int((~np.isnan(est_g)).sum()),
+                   "same_class": float(np.mean(np.isnan(est_p) == np.isnan(est_g))),
+                   "max_abs_diff_1e19": float(agree.max() / 1e19) if agree.size else 0.0,
+                   "within_2tol": float(np.mean(agree <= 2 * TOL)) if agree.size else 1.0},
+        "wall_s": time.time() - t0,
+    }
+
+
+if __name__ == "__main__":
+    import json
+    import sys
+    kw = {}
+    if "--small" in sys.argv:
+        kw = dict(n_train=512, n_test=128, n_search=32, n_flight=5.0e3, search_flight=5.0e3,
+                  train_steps=1500)
+    print(json.dumps(run(**kw)))

@@ -176,3 +176,70 @@ def batched_sweep(n_instances: int = 64, seed: int = 1000, n_steps: int = 10000)
         p["target_in_flight"] = target
         out.append(p)
     return out
+
+
+# ---------------------------------------------------------------- surrogate
+# Ranges of the surrogate's five inputs (the transition search scans the
+# emission flux over [5, 9]e19; the training set brackets it).
+SURROGATE_RANGES = {
+    "gamma_emit": (4.0e19, 1.0e20),      # m^-2 s^-1
+    "T_wall_K": (2000.0, 3000.0),
+    "log10_n_gas": (21.0, 22.0),         # m^-3
+    "gap_m": (1.0e-3, 5.0e-3),
+    "bias_V": (5.0, 30.0),
+}
+SURROGATE_KEYS = tuple(SURROGATE_RANGES)
+
+
+def sobol_settings(n: int, seed: int, keys=SURROGATE_KEYS, fixed=None):
+    """n scrambled-Sobol points over the ranges of ``keys`` (torch's Sobol
+    engine); entries of ``fixed`` are held constant."""
+    import torch
+    eng = torch.quasirandom.SobolEngine(len(keys), scramble=True, seed=seed)
+    u = eng.draw(n).double().numpy()
+    out = []
+    for row in u:
+        s = dict(fixed or {})
+        for k, x in zip(keys, row):
+            lo, hi = SURROGATE_RANGES[k]
+            s[k] = lo + (hi - lo) * float(x)
+        out.append(s)
+    return out
+
+
+def random_settings(n: int, seed: int):
+    """n uniformly random (T_w, n_gas, gap, bias) settings for the transition
+    search (emission flux left free)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        s = {}
+        for k in ("T_wall_K", "log10_n_gas", "gap_m", "bias_V"):
+            lo, hi = SURROGATE_RANGES[k]
+            s[k] = float(rng.uniform(lo, hi))
+        out.append(s)
+    return out
+
+
+def setting_diode(s: dict, n_flight: float = 2.0e4, cell_m: float = 1.0e-5, seed: int = 0,
+                  transits: float = 5.0, window_frac: float = 0.4) -> dict:
+    """He diode of one surrogate setting: cells of ``cell_m``, dt so that an
+    electron at the collision-energy bound crosses at most half a cell, a run
+    of ``transits`` vacuum transit times, the last ``window_frac`` averaged;
+    weight for ~n_flight emitted electrons in flight."""
+    p = he_defaults()
+    gap, V = float(s["gap_m"]), float(s["bias_V"])
+    Nz = max(8, int(round(gap / cell_m)))
+    E_cap = max(60.0, 2.0 * V + 10.0)
+    v_cap = math.sqrt(2.0 * E_cap * E_CHARGE / M_E)
+    dt = min(1e-12, 0.5 * (gap / Nz) / v_cap)
+    t_tr = vacuum_transit_time(gap, V)
+    n_steps = int(math.ceil(transits * t_tr / dt))
+    p.update(L=gap, V=V, Nz=Nz, dt=dt, n_gas=10.0 ** float(s["log10_n_gas"]),
+             T_wall_K=float(s["T_wall_K"]), gamma_emit=float(s["gamma_emit"]),
+             E_cap_e_eV=E_cap, E_cap_i_eV=E_cap, seed=seed, n_steps=n_steps,
+             window_start=int((1.0 - window_frac) * n_steps))
+    p["weight"] = weight_for_in_flight(p["gamma_emit"], gap, V, n_flight)
+    x = p["gamma_emit"] * dt / p["weight"]
+    p["capacity"] = (int(3 * n_flight + 2 * x * 64) + 4096, 16384, 16384)
+    return p
