@@ -37,6 +37,30 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
 
+def measured_traffic():
+    """DRAM bytes per k_push launch from the committed ncu summary, if the
+    kernel source it was taken on is the one built now (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "step_kernels_production_diode.md")
+    csrc = os.path.join(ROOT, "paper_2605_07083_gb300", "csrc")
+    try:
+        h = hashlib.sha1()
+        for f in ("pic_kernels.cu", "pic_internal.cuh"):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+        want = h.hexdigest()[:16]
+        traffic, sha = None, None
+        with open(path) as fh:
+            for line in fh:
+                if line.startswith("traffic_bytes_per_launch(k_push):"):
+                    traffic = float(line.split(":")[1])
+                if line.startswith("kernel_source_sha1_16:"):
+                    sha = line.split(":")[1].strip()
+        return traffic if sha == want else None
+    except OSError:
+        return None
+
+
 def hbm_peak():
     try:
         with open(PEAKS) as f:
@@ -229,7 +253,7 @@ def run_ours(args, rank, world):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": describe(p, n0),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": measured_traffic(),
                      "kernel": "k_push", "peak_kind": peak_kind + " (hbm_gbs)",
                      "alg_bytes_per_particle": ALG_BYTES_PER_PARTICLE,
                      "particles_per_launch": n_per_launch, "avg_launch_ms": push_ms,

@@ -208,56 +208,75 @@ def surrogate_crossing(model, settings, n_grid=161):
 
 
 def guided_search(model, settings, max_err=0.02, **kw):
-    """PIC at the surrogate's crossing +- TOL (or at the endpoints when it
-    predicts none); accepted where PIC confirms the bracket and the surrogate
-    is within max_err of PIC there, otherwise PIC bisection takes over on the
-    bracket the evaluations leave."""
+    """One batched PIC round placed by the surrogate: at its predicted crossing
+    +- TOL, or -- where it predicts none -- once, at the flux where its
+    backflow is closest to 1/2.  A prediction stands when PIC confirms it
+    (same side of 1/2 / bracket confirmed) and the surrogate is within
+    max_err of PIC at every evaluated flux; otherwise PIC bisection takes
+    over on what the evaluations leave."""
     n = len(settings)
     cost = {"gpu_ms": 0.0, "particle_steps": 0, "runs": 0, "rounds": 0}
     pred, bf_grid, grid = surrogate_crossing(model, settings)
     has = ~np.isnan(pred)
-    g_lo = np.where(has, np.clip(pred - TOL, LO, HI), LO)
-    g_hi = np.where(has, np.clip(pred + TOL, LO, HI), HI)
-    bf = _eval(settings + settings, list(g_lo) + list(g_hi), cost, **kw)
-    b_lo, b_hi = bf[:n], bf[n:]
-    s_lo = np.array([np.interp(g_lo[i], grid, bf_grid[i]) for i in range(n)])
-    s_hi = np.array([np.interp(g_hi[i], grid, bf_grid[i]) for i in range(n)])
-    err_ok = (np.abs(s_lo - b_lo) <= max_err) & (np.abs(s_hi - b_hi) <= max_err)
+    # evaluation points: two per predicted crossing, one per predicted absence
+    pts_s, pts_g, owner = [], [], []
+    for i in range(n):
+        if has[i]:
+            for g in (np.clip(pred[i] - TOL, LO, HI), np.clip(pred[i] + TOL, LO, HI)):
+                pts_s.append(settings[i]); pts_g.append(g); owner.append(i)
+        else:
+            k = int(np.argmin(np.abs(bf_grid[i] - 0.5)))
+            pts_s.append(settings[i]); pts_g.append(grid[k]); owner.append(i)
+    bf = _eval(pts_s, pts_g, cost, **kw)
+    pts_g = np.array(pts_g)
+    owner = np.array(owner)
     est = np.full(n, np.nan)
     a = np.full(n, LO)
     b = np.full(n, HI)
     open_ = np.zeros(n, bool)
     fallback = np.zeros(n, bool)
+    err_ok_all = []
     for i in range(n):
-        if b_lo[i] < 0.5 <= b_hi[i]:
-            if has[i] and err_ok[i]:
-                est[i] = 0.5 * (g_lo[i] + g_hi[i])       # bracket of width 2 TOL
-                continue
-            a[i], b[i] = g_lo[i], g_hi[i]
-            open_[i] = b[i] - a[i] > 2 * TOL
-            if not open_[i]:
-                est[i] = 0.5 * (a[i] + b[i])
-            fallback[i] = True
-        elif has[i]:
-            # the crossing is outside the predicted bracket: bisect the rest
-            fallback[i] = True
-            if b_lo[i] >= 0.5:
-                a[i], b[i] = LO, g_lo[i]
+        sel = np.nonzero(owner == i)[0]
+        gi, bi = pts_g[sel], bf[sel]
+        si = np.interp(gi, grid, bf_grid[i])
+        err_ok = bool(np.all(np.abs(si - bi) <= max_err))
+        err_ok_all.append(err_ok)
+        if has[i]:
+            lo_g, hi_g = gi[0], gi[1]
+            if bi[0] < 0.5 <= bi[1]:
+                if err_ok:
+                    est[i] = 0.5 * (lo_g + hi_g)
+                    continue
+                a[i], b[i] = lo_g, hi_g
+            elif bi[0] >= 0.5:
+                a[i], b[i] = LO, lo_g
             else:
-                a[i], b[i] = g_hi[i], HI
-            open_[i] = True
-    if fallback.any():
-        # endpoints of the remaining brackets decide whether a crossing exists
+                a[i], b[i] = hi_g, HI
+        else:
+            same_side = (bi[0] >= 0.5) == (si[0] >= 0.5)
+            if same_side and err_ok:
+                continue                                # no crossing in range, confirmed
+            if bi[0] >= 0.5:
+                a[i], b[i] = LO, gi[0]
+            else:
+                a[i], b[i] = gi[0], HI
+        fallback[i] = True
+        open_[i] = b[i] - a[i] > 2 * TOL
+        if not open_[i]:
+            est[i] = 0.5 * (a[i] + b[i])
+    if open_.any():
+        # the ends of the remaining brackets decide whether a crossing exists
         idx = np.nonzero(open_)[0]
-        if idx.size:
-            bfe = _eval([settings[i] for i in idx] * 2, list(a[idx]) + list(b[idx]), cost, **kw)
-            m = idx.size
-            for k, i in enumerate(idx):
-                if not (bfe[k] < 0.5 <= bfe[m + k]):
-                    open_[i] = False                      # no crossing in range
+        bfe = _eval([settings[i] for i in idx] * 2, list(a[idx]) + list(b[idx]), cost, **kw)
+        m = idx.size
+        for k, i in enumerate(idx):
+            if not (bfe[k] < 0.5 <= bfe[m + k]):
+                open_[i] = False                          # no crossing in range
         _bisect(settings, a, b, open_, est, cost, **kw)
     cost["fallback"] = int(fallback.sum())
-    cost["surrogate_err_ok"] = float(err_ok[has].mean()) if has.any() else 1.0
+    cost["surrogate_err_ok"] = float(np.mean(err_ok_all)) if n else 1.0
+    cost["predicted_crossings"] = int(has.sum())
     return est, cost
 
 
