@@ -159,6 +159,18 @@ static __device__ __noinline__ uint4 philox10_rolled(uint4 c, uint32_t k0, uint3
 
 // Philox2x32-10 word 0 (same paper): one 32x32->64 product per round on a
 // 2-word counter.  The per-particle null-collision candidate word.
+// the same with the ten round keys precomputed (key + r * 0x9E3779B9)
+__device__ __forceinline__ uint32_t philox2x32_w0_rk(uint32_t c0, uint32_t c1,
+                                                     const uint32_t (&rk)[10]) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned long long p = (unsigned long long)0xD256D193u * c0;
+    c0 = (uint32_t)(p >> 32) ^ rk[r] ^ c1;
+    c1 = (uint32_t)p;
+  }
+  return c0;
+}
+
 __device__ __forceinline__ uint32_t philox2x32_w0(uint32_t c0, uint32_t c1, uint32_t k) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
@@ -195,12 +207,17 @@ __device__ __forceinline__ void iso_dir(uint32_t rc, uint32_t rp, float& dx, flo
 
 // Fixed-point cell rule, all FP32 round-to-nearest with no contraction:
 // s = z * inv_dz, j = floor(s) clamped to [0, Nz-1], f = s - j.
+// floor without a conversion: for 0 <= s < 2^22, s + 1.5*2^23 rounded toward
+// zero is 1.5*2^23 + floor(s) (unit spacing there), read from its bits.  A
+// negative or NaN s (never a live particle) maps to a huge unsigned value
+// and is clamped to the last cell, so every index stays in bounds.
 __device__ __forceinline__ void cell_of(float z, float inv_dz, int Nz, int& j, float& f) {
-  float s = __fmul_rn(z, inv_dz);
-  int jj = __float2int_rd(s);
-  jj = min(max(jj, 0), Nz - 1);
-  j = jj;
-  f = __fsub_rn(s, __int2float_rn(jj));
+  const float s = __fmul_rn(z, inv_dz);
+  const float t = __fadd_rz(s, 12582912.0f);
+  unsigned jj = (unsigned)(__float_as_int(t) - 0x4B400000);
+  jj = min(jj, (unsigned)(Nz - 1));
+  j = (int)jj;
+  f = __fsub_rn(s, __int2float_rn((int)jj));
 }
 
 __device__ __forceinline__ long long frac_units(float f) {
@@ -210,7 +227,8 @@ __device__ __forceinline__ long long frac_units(float f) {
 // ---------------------------------------------------------------- bulk copies
 // 1D bulk copies global -> shared completing on an mbarrier (sm_90+ PTX).
 constexpr int kStageBytes = 1536;     // one warp chunk: 128 x (z, v_z, id)
-constexpr int kWaitLimit = 1 << 22;   // bounded mbarrier polls before giving up
+constexpr int kWaitLimit = 1 << 20;   // bounded polls (each suspends up to kSuspendNs)
+constexpr uint32_t kSuspendNs = 1000;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -236,11 +254,16 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// Test a phase; if it is not complete the warp is suspended (it issues
+// nothing) until the phase completes or about kSuspendNs ns pass.
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
+      : "memory");
   return ok != 0u;
 }
 // every wait ends: after kWaitLimit polls the caller gets false

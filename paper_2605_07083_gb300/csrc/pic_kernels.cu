@@ -295,6 +295,7 @@ struct SegCtx {
   float inv_dz, Lf, dt, qmdt;
   int Nz;
   uint32_t tc, ck, stepw;
+  uint32_t rk[10];          // Philox2x32 round keys of the candidate stream
 };
 
 // One particle: gather, leapfrog, wall test and the null-collision candidate
@@ -312,7 +313,7 @@ __device__ __forceinline__ unsigned push_one(const SegCtx& c, const float2* Es2,
   vz = fmaf(c.qmdt, Ez, vz);
   z = fmaf(vz, c.dt, z);
   if (!(z >= 0.0f && z < c.Lf)) return 1u;
-  if (c.tc != 0u && philox2x32_w0(pid, c.stepw, c.ck) < c.tc) return 2u;
+  if (c.tc != 0u && philox2x32_w0_rk(pid, c.stepw, c.rk) < c.tc) return 2u;
   return 0u;
 }
 
@@ -388,9 +389,11 @@ __device__ __forceinline__ void push_body(const DevState& st) {
     }
     hist_zero(hist, icS.Nz);
     __syncthreads();
-    const long long q0 = (lo > s0 ? lo : s0) - s0;
-    const long long q1 = (hi < s1 ? hi : s1) - s0;
-    const long long wq0 = warp_start(q0, q1, warp, W), wq1 = warp_start(q0, q1, warp + 1, W);
+    // quads of this block and warp, relative to the segment: 32-bit (a
+    // segment holds < 2^31 particles)
+    const int q0 = (int)((lo > s0 ? lo : s0) - s0);
+    const int q1 = (int)((hi < s1 ? hi : s1) - s0);
+    const int wq0 = (int)warp_start(q0, q1, warp, W), wq1 = (int)warp_start(q0, q1, warp + 1, W);
     const long long off = st.seg_off[g];
     const int N = st.seg_count[g];
     float* __restrict__ zp = st.z + off;
@@ -408,6 +411,8 @@ __device__ __forceinline__ void push_body(const DevState& st) {
     c.tc = icS.t_cand[sp];
     c.ck = icS.ckey[sp];
     c.stepw = kDepositOnly ? 0u : (uint32_t)st.dyn[inst].step;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) c.rk[r] = c.ck + (uint32_t)r * 0x9E3779B9u;
     uint32_t* dbuf = st.dead_buf + off + 4 * wq0;
     int dead_run = 0;
 
@@ -416,8 +421,8 @@ __device__ __forceinline__ void push_body(const DevState& st) {
     const int nchunks = (int)((wq1 - wq0 + 31) >> 5);
     auto issue = [&](int ch) {
       const int s = ch & 1;
-      const long long qc = wq0 + 32LL * ch;
-      const long long nq = (wq1 - qc) < 32 ? (wq1 - qc) : 32;
+      const int qc = wq0 + 32 * ch;
+      const int nq = (wq1 - qc) < 32 ? (wq1 - qc) : 32;
       const uint32_t bytes = (uint32_t)nq * 16u;
       unsigned char* b = wstage + s * kStageBytes;
       fence_proxy_async();
@@ -431,8 +436,8 @@ __device__ __forceinline__ void push_body(const DevState& st) {
       if (nchunks > 1) issue(1);
     }
     int ch = 0;
-    for (long long base = wq0; base < wq1; base += 32, ++ch) {
-      const long long q = base + lane;
+    for (int base = wq0; base < wq1; base += 32, ++ch) {
+      const int q = base + lane;
       unsigned dm = 0, cm = 0, am = 0;
       float zz[4] = {0.0f, 0.0f, 0.0f, 0.0f};
       float4 z4s = make_float4(0.f, 0.f, 0.f, 0.f), v4s = z4s;
@@ -457,7 +462,7 @@ __device__ __forceinline__ void push_body(const DevState& st) {
         if (lane == 0 && ch + 2 < nchunks) issue(ch + 2);
       }
       if (q < wq1) {
-        const long long i = 4 * q;
+        const int i = 4 * q;
         if (i + 3 < N) {
           float4 z4 = kDepositOnly ? __ldcs(reinterpret_cast<const float4*>(zp + i)) : z4s;
           if (kDepositOnly) {
@@ -555,7 +560,7 @@ __device__ __forceinline__ void push_body(const DevState& st) {
   }
 }
 
-__global__ void __launch_bounds__(256, 4) k_push(DevState st) { push_body<false>(st); }
+__global__ void __launch_bounds__(256, 3) k_push(DevState st) { push_body<false>(st); }
 __global__ void k_deposit(DevState st) { push_body<true>(st); }
 
 // ------------------------------------------------------------------ field solve
