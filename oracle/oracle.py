@@ -8,6 +8,7 @@ wraps it with numpy.  It imports nothing from the CUDA library package.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -114,6 +115,10 @@ def lib():
                                           C.c_uint32, C.c_uint32, P, P]
             L.oracle_postprocess.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double,
                                              P, P, C.c_double, C.POINTER(ODiag)]
+            L.oracle_species_fixed.argtypes = [P, C.c_int, P]
+            L.oracle_set_profile_period.argtypes = [P, C.c_int64]
+            L.oracle_profiles.restype = C.c_int64
+            L.oracle_profiles.argtypes = [P, P, P]
             L.oracle_sigma_exc.restype = C.c_double
             L.oracle_sigma_exc.argtypes = [C.POINTER(OCfg), C.c_double]
             L.oracle_sigma_iz.restype = C.c_double
@@ -204,6 +209,24 @@ class Oracle:
         self._L.oracle_field(self._h, _ptr(phi), _ptr(E))
         return phi, E
 
+    def species_fixed(self, species):
+        out = np.empty(self.params["Nz"] + 1, np.int64)
+        self._L.oracle_species_fixed(self._h, species, _ptr(out))
+        return out
+
+    def set_profile_period(self, period):
+        """Sample profiles every `period` steps inside the window (0 = off);
+        clears the sums."""
+        self._L.oracle_set_profile_period(self._h, int(period))
+
+    def profiles(self):
+        """(phi_sum [Nz+1], counts [3, Nz+1] int64, samples)."""
+        n = self.params["Nz"] + 1
+        phi = np.zeros(n, np.float64)
+        cnt = np.zeros((3, n), np.int64)
+        k = self._L.oracle_profiles(self._h, _ptr(phi), _ptr(cnt))
+        return phi, cnt, int(k)
+
     def tallies(self) -> dict:
         t = OTally()
         self._L.oracle_tallies(self._h, C.byref(t))
@@ -286,3 +309,46 @@ def sigma_exc(params: dict, E_eV: float) -> float:
 def sigma_iz(params: dict, E_eV: float) -> float:
     c = make_cfg(params)
     return lib().oracle_sigma_iz(C.byref(c), E_eV)
+
+
+def profile_averages(phi_sum, counts, samples, weight, L, Nz):
+    """Late-time averages (Sec. 3) from sampled sums.
+
+    phi_avg = phi_sum / K in V.  Number density of species s at node j:
+    counts[s, j] / 2^24 particles times the weight w, divided by K and by the
+    node's length, dz inside and dz / 2 at the two electrodes (the boundary
+    node collects charge from half a cell only)."""
+    if samples <= 0:
+        raise ValueError("no samples")
+    dz = L / Nz
+    vol = np.full(Nz + 1, dz)
+    vol[0] = vol[-1] = 0.5 * dz
+    phi = np.asarray(phi_sum, np.float64) / samples
+    dens = np.asarray(counts, np.float64) / 16777216.0 * weight / (samples * vol)
+    return phi, dens
+
+
+def virtual_cathode(phi_avg, L, T_emit_eV, net_efficiency, near_fraction=0.1) -> dict:
+    """Eq. 9-10 of Sec. 3.
+
+    Eq. 10 maps the window's net transport efficiency to an effective
+    barrier, phi_vc_eff = T_emit ln(Gamma_net / Gamma_emit) (NaN when the
+    efficiency is not positive).  The near-cathode minimum phi_min of the
+    averaged potential is taken over the nodes j <= floor(near_fraction Nz)
+    (at least node 1); Eq. 9 gives its transmission eta_VC = exp((phi_min -
+    phi_w) / T_emit) with the wall at phi_w = 0."""
+    phi = np.asarray(phi_avg, np.float64)
+    Nz = phi.size - 1
+    jmax = min(Nz, max(1, int(math.floor(near_fraction * Nz))))
+    seg = phi[:jmax + 1]
+    j = int(np.argmin(seg))
+    phi_min = float(seg[j])
+    eff = float(net_efficiency)
+    return {
+        "T_emit_eV": float(T_emit_eV),
+        "net_efficiency": eff,
+        "phi_vc_eff": T_emit_eV * math.log(eff) if eff > 0 else float("nan"),
+        "phi_min": phi_min,
+        "z_min": j * (L / Nz),
+        "eta_vc": math.exp(phi_min / T_emit_eV),
+    }

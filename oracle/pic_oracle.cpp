@@ -11,6 +11,8 @@
  *             partner drawn at T_n,e / T_n,i, optional excitation channel
  *   Sec. 2.3  Gamma_net = Gamma_emit - Gamma_ref, backflow ratio
  *   Sec. 2.4  Eq. 1-8 boundary energy diagnostics
+ *   Sec. 3    late-time averaged potential profile (the input of Eq. 9-10)
+ *             and per-species density profiles, sampled every `period` steps
  * Readings where the paper is silent are listed in the repository design
  * notes; each is marked "reading" below.
  *
@@ -144,6 +146,11 @@ struct oracle_sim {
     int64_t step;
     otally win;
     std::vector<oevent> events;
+    /* sampled profiles (0 = off) */
+    int64_t prof_period = 0;
+    int64_t prof_n = 0;
+    std::vector<double> phi_sum;     /* [Nz+1] */
+    std::vector<int64_t> prof;       /* [3][Nz+1] */
 };
 
 /* ------------------------------------------------------------------------ */
@@ -369,6 +376,19 @@ void deposit(const oracle_sim* s, std::vector<int64_t>& rho) {
     }
 }
 
+/* Linear-weight deposit of one species without charge sign or weight:
+ * every particle puts 2^24 units on its two nodes (same cell rule). */
+void deposit_species(const oracle_sim* s, int k, int64_t* out) {
+    const int Nz = s->c.Nz;
+    for (int j = 0; j <= Nz; ++j) out[j] = 0;
+    const Species& p = s->sp[k];
+    for (size_t i = 0; i < p.size(); ++i) {
+        CellW cw = cell_of((float)p.z[i], s->inv_dz_f, Nz);
+        out[cw.j] += (int64_t)(1 << 24) - cw.Q;
+        out[cw.j + 1] += cw.Q;
+    }
+}
+
 /* Sec. 2.1: phi from rho each step, E = -dphi/dz (central inside, one-sided
  * at the electrodes -- reading). */
 void field(const oracle_sim* s, const std::vector<int64_t>& rho, std::vector<double>& phi,
@@ -571,6 +591,21 @@ void do_step(oracle_sim* s) {
     }
     if (in_win) s->win.steps += 1;
     s->step = n + 1;
+    /* profile sample of the state after step n (reading: the steps n >=
+     * window_start with (n - window_start) a multiple of the period) */
+    if (s->prof_period > 0 && n >= c.window_start && (n - c.window_start) % s->prof_period == 0) {
+        std::vector<int64_t> rho;
+        std::vector<double> ph, e;
+        deposit(s, rho);
+        field(s, rho, ph, e);
+        for (int j = 0; j <= Nz; ++j) s->phi_sum[j] += ph[j];
+        std::vector<int64_t> cnt(Nz + 1);
+        for (int k = 0; k < 3; ++k) {
+            deposit_species(s, k, cnt.data());
+            for (int j = 0; j <= Nz; ++j) s->prof[(size_t)k * (Nz + 1) + j] += cnt[j];
+        }
+        s->prof_n += 1;
+    }
 }
 
 }  // namespace
@@ -608,6 +643,27 @@ void oracle_diag(const oracle_sim* s, odiag* out) {
     double T = (double)s->win.steps * s->c.dt;
     double Tc = kKb * s->c.T_wall_K / kQe;
     oracle_postprocess(s->c.gamma_emit, Tc, s->c.weight, T, cnt, ke, (double)s->win.emitted, out);
+}
+
+void oracle_species_fixed(const oracle_sim* s, int species, int64_t* out) {
+    if (species < 0 || species > 2) return;
+    deposit_species(s, species, out);
+}
+
+void oracle_set_profile_period(oracle_sim* s, int64_t period) {
+    const int Nz = s->c.Nz;
+    s->prof_period = period > 0 ? period : 0;
+    s->prof_n = 0;
+    s->phi_sum.assign(Nz + 1, 0.0);
+    s->prof.assign((size_t)3 * (Nz + 1), 0);
+}
+
+int64_t oracle_profiles(const oracle_sim* s, double* phi_sum, int64_t* counts) {
+    if (phi_sum && !s->phi_sum.empty())
+        std::memcpy(phi_sum, s->phi_sum.data(), s->phi_sum.size() * sizeof(double));
+    if (counts && !s->prof.empty())
+        std::memcpy(counts, s->prof.data(), s->prof.size() * sizeof(int64_t));
+    return s->prof_n;
 }
 
 int64_t oracle_events(const oracle_sim* s, oevent* out, int64_t cap) {

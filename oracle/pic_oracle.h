@@ -119,6 +119,17 @@ int64_t oracle_events(const oracle_sim* s, oevent* out, int64_t cap);
 void    oracle_derived(const oracle_sim* s, double* nu_max, uint32_t* t_cand,
                        double* emit_x, uint32_t* t_frac);
 
+/* Per-species linear-weight deposit of the current state, 2^24 units per
+ * particle, no charge sign or weight (Nz+1 values). */
+void    oracle_species_fixed(const oracle_sim* s, int species, int64_t* out);
+/* Sampled profiles (Sec. 3 averaged potential; reading): after every step n
+ * with n >= window_start and (n - window_start) % period == 0, phi of the
+ * state after the step is added to phi_sum[Nz+1] and each species' deposit
+ * to counts[3][Nz+1].  Setting the period (0 = off) clears the sums. */
+void    oracle_set_profile_period(oracle_sim* s, int64_t period);
+/* copies the sums (either pointer may be NULL); returns the sample count */
+int64_t oracle_profiles(const oracle_sim* s, double* phi_sum, int64_t* counts);
+
 /* ---- stand-alone pieces, exposed for pinning tests ---- */
 void    oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 /* word 0 of Philox2x32-10 of counter (c0, c1) under key */
