@@ -200,6 +200,78 @@ int pic_get_rho_fixed(pic_handle* h, int instance, int64_t* out, int64_t n_nodes
  * for the current state; either pointer may be NULL.  Synchronises. */
 int pic_get_field(pic_handle* h, int instance, double* phi, float* E, int64_t n_nodes);
 
+/* ---- late-time profiles and the virtual-cathode estimate (Sec. 3) -----
+ * Sec. 3 reads the diode state off late-time averaged potential profiles and
+ * compares the net transport efficiency with a virtual-cathode transmission
+ * estimate (Eq. 9-10).  Sampling rule: after every step n with n >=
+ * window_start and (n - window_start) % period == 0, the potential of the new
+ * state and, per species, the linear-weight deposit of its particles are added
+ * to per-node sums on the device. */
+
+/* Turn sampling on (period >= 1) or off (0) for every instance; clears the
+ * sums either way.  The first call with period >= 1 allocates 32 bytes per
+ * node.  While on, each step launches one more kernel, which returns at once
+ * on steps that are not samples. */
+int pic_set_profile_period(pic_handle* h, int64_t period);
+
+/* Averages over the K samples taken so far by one instance, on its
+ * n_nodes = n_cells + 1 nodes.  Any output may be NULL.
+ *   phi_avg[j]             mean potential, V
+ *   density[s*n_nodes + j] mean number density of species s, m^-3: the
+ *                          sampled linear weights times the macro weight over
+ *                          the node's length (dz inside, dz/2 at electrodes)
+ *   counts[s*n_nodes + j]  the exact sums behind density, 2^24 units per
+ *                          particle (bit-exact test hook)
+ *   *n_samples             K
+ * With K = 0 the averages are NaN.  PIC_EINVAL if sampling was never turned
+ * on or n_nodes != n_cells + 1.  Synchronises. */
+int pic_get_profiles(pic_handle* h, int instance, int64_t n_nodes, double* phi_avg,
+                     double* density, int64_t* counts, int64_t* n_samples);
+
+/* Eq. 9-10 of one instance, from the window tallies and the averaged phi. */
+typedef struct pic_vc {
+    int64_t samples;          /* profile samples behind phi_min */
+    double T_emit_eV;         /* k T_wall / e */
+    double net_efficiency;    /* Gamma_net / Gamma_emit over the window */
+    double phi_vc_eff;        /* Eq. 10: T_emit ln(Gamma_net / Gamma_emit), V; NaN if <= 0 */
+    double phi_min;           /* minimum of the averaged phi over the nodes
+                                 j <= floor(near_fraction * n_cells) (at least
+                                 nodes 0 and 1), V; <= 0 since phi_0 = 0 */
+    double z_min;             /* position of the first node holding it, m */
+    double eta_vc;            /* Eq. 9 at phi_min, wall phi_w = 0: exp(phi_min / T_emit) */
+} pic_vc;
+
+/* near_fraction in (0, 1].  PIC_EINVAL without profile samples.
+ * Synchronises. */
+int pic_virtual_cathode(pic_handle* h, int instance, double near_fraction, pic_vc* out);
+
+/* ---- checkpoint / resume ---------------------------------------------
+ * The paper's production runs take 4.5e6 steps (Sec. 3); a run can be cut
+ * into pieces.  A checkpoint holds the whole handle: every instance's live
+ * particles in array order, step index, id counter, window tallies and
+ * profile sums.  Every random draw is keyed by (seed, species, particle id,
+ * step) and the charge deposit is exact integer arithmetic, so a handle that
+ * loads a checkpoint continues bit for bit as the uninterrupted run would,
+ * given the same launch shape (pic_tune).  The byte format is private to the
+ * library, versioned, and checked on load. */
+
+/* Bytes pic_save needs for the current state.  Synchronises. */
+int pic_checkpoint_bytes(pic_handle* h, size_t* bytes);
+
+/* Write the state to a host buffer of `bytes` bytes; *written (may be NULL)
+ * receives the size used.  PIC_ECAPACITY if the buffer is too small (nothing
+ * written).  Synchronises. */
+int pic_save(pic_handle* h, void* host_buf, size_t bytes, size_t* written);
+
+/* Replace the state of a handle with a checkpoint of `bytes` bytes (at least
+ * what pic_save wrote).  The handle must have been
+ * created with the same instance count, configurations (every pic_config
+ * field but size and reserved0) and resolved capacities; otherwise, or if
+ * the buffer is not a checkpoint of this library version, PIC_EINVAL and the
+ * handle is unchanged.  Profile sampling takes the checkpoint's period.
+ * Synchronises. */
+int pic_load(pic_handle* h, const void* host_buf, size_t bytes);
+
 /* Set the step index of every instance (Philox counters use it). */
 int pic_set_step(pic_handle* h, int64_t step);
 
@@ -284,7 +356,7 @@ void pic_destroy(pic_handle* h);
 const char* pic_strerror(int code);
 int pic_abi_version(void);
 /* sizeof of the ABI structs for foreign bindings: 0 pic_config, 1 pic_tuning,
- * 2 pic_diag, 3 pic_profile; 0 for anything else. */
+ * 2 pic_diag, 3 pic_profile, 4 pic_vc; 0 for anything else. */
 size_t pic_sizeof(int which);
 
 #ifdef __cplusplus

@@ -21,6 +21,7 @@ __global__ void k_deposit(DevState st);
 __global__ void k_mcc(DevState st);
 __global__ void k_post(DevState st);
 __global__ void k_field(DevState st);
+__global__ void k_profile(DevState st);
 __global__ void k_fill_ids(uint32_t* id, long long n, uint32_t first);
 __global__ void k_count_outside(const float* z, long long n, float Lf, int* bad);
 void sort_launch(const DevState& st, int max_chunks, int max_nz, cudaStream_t s);
@@ -75,6 +76,8 @@ struct pic_handle {
   int mcc_blocks = 0;
   bool sort_ready = false;
   int sort_chunks = 1;
+  int prof_gx = 1;              // k_profile blocks per segment
+  size_t prof_smem = 0;
   char last_error[256] = {0};
 };
 
@@ -251,7 +254,7 @@ cudaError_t raise_smem_limits(int device) {
   cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   if (e != cudaSuccess) return e;
   const void* fns[] = {(const void*)k_push, (const void*)k_deposit, (const void*)k_field,
-                       (const void*)k_post};
+                       (const void*)k_post, (const void*)k_profile};
   for (const void* f : fns) {
     e = set_dynamic_smem_limit(f, optin);
     if (e != cudaSuccess) return e;
@@ -290,6 +293,15 @@ int set_launch_shape(pic_handle* h) {
   const size_t species = (size_t)kDeadSmem * 4 + (size_t)(h->G + 1) * 12 + 16;
   const size_t tail = (size_t)h->max_nodes * 32 + 8 + (size_t)kEvCap * 8;
   h->post_smem = std::max(species, tail);
+  // profile sampler: blocks per segment so that none bins more than 2^20
+  // particles (its 32-bit counters), else about two blocks per SM in total
+  int64_t max_cap = 1;
+  for (int32_t c : h->seg_cap) max_cap = std::max<int64_t>(max_cap, c);
+  const int64_t gmin = (max_cap + (1 << 20) - 1) >> 20;
+  const int64_t gfill = std::min<int64_t>((max_cap + 8191) / 8192,
+                                          std::max<int64_t>(1, 2 * h->sm_count / h->n_seg));
+  h->prof_gx = (int)std::max<int64_t>(1, std::max(gmin, gfill));
+  h->prof_smem = (size_t)(h->max_nodes - 1) * 12;
   drop_graph(h);
   return PIC_OK;
 }
@@ -345,11 +357,18 @@ bool sort_due(const pic_handle* h, int64_t step_after) {
   return h->sort_period > 0 && step_after % h->sort_period == 0;
 }
 
+// the profile sampler after a step (device-side test of the sampling rule)
+void launch_profile(pic_handle* h) {
+  if (h->st.prof_period > 0)
+    k_profile<<<dim3((unsigned)h->prof_gx, (unsigned)h->n_seg), 256, h->prof_smem, h->stream>>>(h->st);
+}
+
 // one time step; the sort, when due, follows the step
 cudaError_t launch_step(pic_handle* h) {
   k_push<<<h->G, h->push_threads, h->push_smem, h->stream>>>(h->st);
   k_mcc<<<h->mcc_blocks, kMccThreads, 0, h->stream>>>(h->st);
   k_post<<<3 * h->n_inst, kPostThreads, h->post_smem, h->stream>>>(h->st);
+  launch_profile(h);
   h->host_step += 1;
   if (sort_due(h, h->host_step)) launch_sort(h);
   return cudaGetLastError();
@@ -365,6 +384,7 @@ int build_graph(pic_handle* h, int len) {
     k_push<<<h->G, h->push_threads, h->push_smem, h->stream>>>(h->st);
     k_mcc<<<h->mcc_blocks, kMccThreads, 0, h->stream>>>(h->st);
     k_post<<<3 * h->n_inst, kPostThreads, h->post_smem, h->stream>>>(h->st);
+    launch_profile(h);
     if (sort_due(h, saved + i + 1)) launch_sort(h);
   }
   e = cudaStreamEndCapture(h->stream, &g);
@@ -453,6 +473,7 @@ size_t pic_sizeof(int which) {
     case 1: return sizeof(pic_tuning);
     case 2: return sizeof(pic_diag);
     case 3: return sizeof(pic_profile);
+    case 4: return sizeof(pic_vc);
     default: return 0;
   }
 }
@@ -712,9 +733,10 @@ int pic_profile_steps(pic_handle* h, int64_t n_steps, pic_profile* out) {
     k_mcc<<<h->mcc_blocks, kMccThreads, 0, h->stream>>>(h->st);
     cudaEventRecord(e[5], h->stream);
     k_post<<<3 * h->n_inst, kPostThreads, h->post_smem, h->stream>>>(h->st);
+    launch_profile(h);
     cudaEventRecord(e[2], h->stream);
     h->host_step += 1;
-    out->launches += 3;
+    out->launches += h->st.prof_period > 0 ? 4 : 3;
     out->push_launches += 1;
     if (sort_due(h, h->host_step)) {
       cudaEventRecord(e[3], h->stream);
@@ -821,6 +843,279 @@ int pic_get_field(pic_handle* h, int instance, double* phi, float* E, int64_t n_
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e);
   return check_flags(h);
+}
+
+int pic_set_profile_period(pic_handle* h, int64_t period) {
+  if (!h || period < 0) return PIC_EINVAL;
+  if (h->sticky != PIC_OK) return h->sticky;
+  const size_t tn = (size_t)h->total_nodes;
+  const size_t bytes = sizeof(double) * tn + sizeof(long long) * 3 * tn + sizeof(long long) * h->n_inst;
+  if (period > 0 && !h->st.phi_sum) {
+    void* p = dev_alloc(h, bytes);
+    if (!p) return PIC_ENOMEM;
+    h->st.phi_sum = (double*)p;
+    h->st.prof = (int64_t*)(h->st.phi_sum + tn);
+    h->st.prof_n = h->st.prof + 3 * tn;
+    h->st.tn = h->total_nodes;
+  }
+  if (h->st.phi_sum) {
+    cudaError_t e = cudaMemsetAsync(h->st.phi_sum, 0, bytes, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+  }
+  h->st.prof_period = period;
+  drop_graph(h);
+  return PIC_OK;
+}
+
+int pic_get_profiles(pic_handle* h, int instance, int64_t n_nodes, double* phi_avg,
+                     double* density, int64_t* counts, int64_t* n_samples) {
+  if (!h || instance < 0 || instance >= h->n_inst || !h->st.phi_sum) return PIC_EINVAL;
+  const pic_config& c = h->cfg[instance];
+  const int nn = c.n_cells + 1;
+  if (n_nodes != nn) return PIC_EINVAL;
+  const int off = h->ic[instance].node_off;
+  std::vector<double> ps(nn);
+  std::vector<long long> cnt(3 * (size_t)nn);
+  long long K = 0;
+  cudaError_t e = cudaMemcpyAsync(ps.data(), h->st.phi_sum + off, sizeof(double) * nn,
+                                  cudaMemcpyDeviceToHost, h->stream);
+  for (int sp = 0; sp < 3 && e == cudaSuccess; ++sp)
+    e = cudaMemcpyAsync(cnt.data() + (size_t)sp * nn, h->st.prof + (size_t)sp * h->st.tn + off,
+                        sizeof(long long) * nn, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&K, h->st.prof_n + instance, sizeof(long long), cudaMemcpyDeviceToHost,
+                        h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  if (n_samples) *n_samples = K;
+  if (counts)
+    for (size_t i = 0; i < cnt.size(); ++i) counts[i] = cnt[i];
+  const double nan = std::nan("");
+  const double dz = c.gap_m / c.n_cells;
+  if (phi_avg)
+    for (int j = 0; j < nn; ++j) phi_avg[j] = K > 0 ? ps[j] / (double)K : nan;
+  if (density)
+    for (int sp = 0; sp < 3; ++sp)
+      for (int j = 0; j < nn; ++j) {
+        // linear weights of the node's particles over its length: dz inside,
+        // dz/2 at the electrodes
+        const double len = (j == 0 || j == nn - 1) ? 0.5 * dz : dz;
+        density[(size_t)sp * nn + j] =
+            K > 0 ? (double)cnt[(size_t)sp * nn + j] / (double)kTwo24 * c.weight / ((double)K * len) : nan;
+      }
+  return check_flags(h);
+}
+
+int pic_virtual_cathode(pic_handle* h, int instance, double near_fraction, pic_vc* out) {
+  if (!h || !out || instance < 0 || instance >= h->n_inst || !(near_fraction > 0.0) ||
+      near_fraction > 1.0)
+    return PIC_EINVAL;
+  const pic_config& c = h->cfg[instance];
+  const int nn = c.n_cells + 1;
+  std::vector<double> phi(nn);
+  int64_t K = 0;
+  int rc = pic_get_profiles(h, instance, nn, phi.data(), nullptr, nullptr, &K);
+  if (rc != PIC_OK) return rc;
+  if (K <= 0) return PIC_EINVAL;
+  pic_diag d;
+  rc = pic_diagnostics(h, instance, &d);
+  if (rc != PIC_OK) return rc;
+  std::memset(out, 0, sizeof(*out));
+  out->samples = K;
+  out->T_emit_eV = d.T_c_eV;
+  out->net_efficiency = d.net_efficiency;
+  // Eq. 10: the efficiency mapped to an equivalent barrier
+  out->phi_vc_eff = d.net_efficiency > 0 ? d.T_c_eV * std::log(d.net_efficiency) : std::nan("");
+  // near-cathode minimum of the averaged potential and its Eq. 9 transmission
+  const int jmax = std::min(c.n_cells, std::max(1, (int)std::floor(near_fraction * c.n_cells)));
+  int jm = 0;
+  for (int j = 1; j <= jmax; ++j)
+    if (phi[j] < phi[jm]) jm = j;
+  out->phi_min = phi[jm];
+  out->z_min = jm * (c.gap_m / c.n_cells);
+  out->eta_vc = std::exp(out->phi_min / d.T_c_eV);
+  return PIC_OK;
+}
+
+namespace {
+
+struct CkptHeader {
+  char magic[8];
+  uint32_t abi, cfg_bytes, dyn_bytes, reserved;
+  int32_t n_inst, n_seg, total_nodes, has_prof;
+  int64_t prof_period, step;
+};
+const char kCkptMagic[8] = {'P', 'I', 'C', 'C', 'K', 'P', 'T', '1'};
+
+// the fields that define a run: all but size, reserved0 and capacity
+pic_config run_fields(pic_config c) {
+  c.size = 0;
+  c.reserved0 = 0;
+  c.capacity[0] = c.capacity[1] = c.capacity[2] = 0;
+  return c;
+}
+
+size_t ckpt_bytes(const pic_handle* h, const std::vector<int32_t>& counts, bool prof) {
+  size_t b = sizeof(CkptHeader) + sizeof(pic_config) * h->n_inst + sizeof(int32_t) * 2 * h->n_seg +
+             sizeof(InstDyn) * h->n_inst;
+  for (int32_t n : counts) b += (size_t)n * 20;
+  if (prof) b += sizeof(double) * h->total_nodes + sizeof(long long) * (3 * (size_t)h->total_nodes + h->n_inst);
+  return b;
+}
+
+int read_counts(pic_handle* h, std::vector<int32_t>& counts) {
+  counts.resize(h->n_seg);
+  cudaError_t e = cudaMemcpyAsync(counts.data(), h->st.seg_count, sizeof(int32_t) * h->n_seg,
+                                  cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? PIC_OK : cuda_fail(h, e);
+}
+
+}  // namespace
+
+int pic_checkpoint_bytes(pic_handle* h, size_t* bytes) {
+  if (!h || !bytes) return PIC_EINVAL;
+  std::vector<int32_t> counts;
+  int rc = read_counts(h, counts);
+  if (rc != PIC_OK) return rc;
+  *bytes = ckpt_bytes(h, counts, h->st.phi_sum != nullptr);
+  return check_flags(h);
+}
+
+int pic_save(pic_handle* h, void* host_buf, size_t bytes, size_t* written) {
+  if (!h || !host_buf) return PIC_EINVAL;
+  if (h->sticky != PIC_OK) return h->sticky;
+  std::vector<int32_t> counts;
+  int rc = read_counts(h, counts);
+  if (rc != PIC_OK) return rc;
+  const bool prof = h->st.phi_sum != nullptr;
+  const size_t need = ckpt_bytes(h, counts, prof);
+  if (bytes < need) return PIC_ECAPACITY;
+  std::vector<InstDyn> dyn(h->n_inst);
+  cudaError_t e = cudaMemcpyAsync(dyn.data(), h->st.dyn, sizeof(InstDyn) * h->n_inst,
+                                  cudaMemcpyDeviceToHost, h->stream);
+  char* p = (char*)host_buf;
+  CkptHeader hd;
+  std::memset(&hd, 0, sizeof(hd));
+  std::memcpy(hd.magic, kCkptMagic, 8);
+  hd.abi = PIC_ABI_VERSION;
+  hd.cfg_bytes = sizeof(pic_config);
+  hd.dyn_bytes = sizeof(InstDyn);
+  hd.n_inst = h->n_inst;
+  hd.n_seg = h->n_seg;
+  hd.total_nodes = h->total_nodes;
+  hd.has_prof = prof ? 1 : 0;
+  hd.prof_period = h->st.prof_period;
+  hd.step = h->host_step;
+  std::memcpy(p, &hd, sizeof(hd));
+  p += sizeof(hd);
+  std::memcpy(p, h->cfg.data(), sizeof(pic_config) * h->n_inst);
+  p += sizeof(pic_config) * h->n_inst;
+  std::memcpy(p, h->seg_cap.data(), sizeof(int32_t) * h->n_seg);
+  p += sizeof(int32_t) * h->n_seg;
+  std::memcpy(p, counts.data(), sizeof(int32_t) * h->n_seg);
+  p += sizeof(int32_t) * h->n_seg;
+  char* dyn_at = p;
+  p += sizeof(InstDyn) * h->n_inst;
+  for (int g = 0; g < h->n_seg && e == cudaSuccess; ++g) {
+    const size_t n = (size_t)counts[g], b = 4 * n;
+    const int64_t o = h->seg_off[g];
+    if (n == 0) continue;
+    e = cudaMemcpyAsync(p, h->st.z + o, b, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p + b, h->st.vx + o, b, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p + 2 * b, h->st.vy + o, b, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p + 3 * b, h->st.vz + o, b, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p + 4 * b, h->st.id + o, b, cudaMemcpyDeviceToHost, h->stream);
+    p += 5 * b;
+  }
+  if (prof && e == cudaSuccess) {
+    const size_t tn = (size_t)h->total_nodes;
+    const size_t b = sizeof(double) * tn + sizeof(long long) * (3 * tn + h->n_inst);
+    e = cudaMemcpyAsync(p, h->st.phi_sum, b, cudaMemcpyDeviceToHost, h->stream);
+    p += b;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  std::memcpy(dyn_at, dyn.data(), sizeof(InstDyn) * h->n_inst);
+  if (written) *written = (size_t)(p - (char*)host_buf);
+  return check_flags(h);
+}
+
+int pic_load(pic_handle* h, const void* host_buf, size_t bytes) {
+  if (!h || !host_buf || bytes < sizeof(CkptHeader)) return PIC_EINVAL;
+  if (h->sticky != PIC_OK) return h->sticky;
+  const char* p = (const char*)host_buf;
+  const char* end = p + bytes;
+  CkptHeader hd;
+  std::memcpy(&hd, p, sizeof(hd));
+  p += sizeof(hd);
+  if (std::memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.abi != PIC_ABI_VERSION ||
+      hd.cfg_bytes != sizeof(pic_config) || hd.dyn_bytes != sizeof(InstDyn) ||
+      hd.n_inst != h->n_inst || hd.n_seg != h->n_seg || hd.total_nodes != h->total_nodes ||
+      hd.prof_period < 0 || hd.step < 0)
+    return PIC_EINVAL;
+  const size_t fixed = sizeof(pic_config) * h->n_inst + sizeof(int32_t) * 2 * h->n_seg +
+                       sizeof(InstDyn) * h->n_inst;
+  if ((size_t)(end - p) < fixed) return PIC_EINVAL;
+  for (int i = 0; i < h->n_inst; ++i) {
+    pic_config a, b = run_fields(h->cfg[i]);
+    std::memcpy(&a, p + sizeof(pic_config) * i, sizeof(pic_config));
+    a = run_fields(a);
+    if (std::memcmp(&a, &b, sizeof(pic_config)) != 0) return PIC_EINVAL;
+  }
+  p += sizeof(pic_config) * h->n_inst;
+  if (std::memcmp(p, h->seg_cap.data(), sizeof(int32_t) * h->n_seg) != 0) return PIC_EINVAL;
+  p += sizeof(int32_t) * h->n_seg;
+  std::vector<int32_t> counts(h->n_seg);
+  std::memcpy(counts.data(), p, sizeof(int32_t) * h->n_seg);
+  p += sizeof(int32_t) * h->n_seg;
+  std::vector<InstDyn> dyn(h->n_inst);
+  std::memcpy(dyn.data(), p, sizeof(InstDyn) * h->n_inst);
+  p += sizeof(InstDyn) * h->n_inst;
+  for (int g = 0; g < h->n_seg; ++g)
+    if (counts[g] < 0 || counts[g] > h->seg_cap[g]) return PIC_EINVAL;
+  for (const InstDyn& d : dyn)
+    if (d.step != hd.step) return PIC_EINVAL;
+  if (ckpt_bytes(h, counts, hd.has_prof != 0) > bytes) return PIC_EINVAL;
+  // validated: from here on the handle takes the checkpoint's state
+  if (hd.has_prof) {
+    if (!h->st.phi_sum) {          // allocate the sums (overwritten below)
+      int rc = pic_set_profile_period(h, 1);
+      if (rc != PIC_OK) return rc;
+    }
+    h->st.prof_period = hd.prof_period;
+  } else {
+    int rc = pic_set_profile_period(h, 0);
+    if (rc != PIC_OK) return rc;
+  }
+  cudaError_t e = cudaMemcpyAsync(h->st.seg_count, counts.data(), sizeof(int32_t) * h->n_seg,
+                                  cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->st.dyn, dyn.data(), sizeof(InstDyn) * h->n_inst, cudaMemcpyHostToDevice,
+                        h->stream);
+  for (int g = 0; g < h->n_seg && e == cudaSuccess; ++g) {
+    const size_t n = (size_t)counts[g], b = 4 * n;
+    const int64_t o = h->seg_off[g];
+    if (n == 0) continue;
+    e = cudaMemcpyAsync(h->st.z + o, p, b, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->st.vx + o, p + b, b, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->st.vy + o, p + 2 * b, b, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->st.vz + o, p + 3 * b, b, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->st.id + o, p + 4 * b, b, cudaMemcpyHostToDevice, h->stream);
+    p += 5 * b;
+  }
+  if (hd.has_prof && e == cudaSuccess) {
+    const size_t tn = (size_t)h->total_nodes;
+    const size_t b = sizeof(double) * tn + sizeof(long long) * (3 * tn + h->n_inst);
+    e = cudaMemcpyAsync(h->st.phi_sum, p, b, cudaMemcpyHostToDevice, h->stream);
+    p += b;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  h->host_step = hd.step;
+  h->dirty = true;               // charge and field are recomputed from the particles
+  drop_graph(h);
+  return PIC_OK;
 }
 
 int pic_tune(pic_handle* h, const pic_tuning* t) {

@@ -124,7 +124,19 @@ struct DevState {
   const InstConst* ic;
   InstDyn* dyn;
   PostScratch* post;       // [n_inst]
+  // late-time profiles (sampled every prof_period steps of the window; 0 = off)
+  long long prof_period;
+  int tn;                  // total node slots over all instances (stride of prof)
+  double* phi_sum;         // [tn] sum of sampled phi
+  int64_t* prof;           // [3][tn] sum of sampled species deposits, 2^24 units per particle
+  int64_t* prof_n;         // [n_inst] samples taken
 };
+
+// Is the state after step n a profile sample?  (Sec. 3 late-time averages:
+// steps n >= window_start with (n - window_start) a multiple of the period.)
+__device__ __forceinline__ bool profile_due(long long period, long long window_start, long long n) {
+  return period > 0 && n >= window_start && (n - window_start) % period == 0;
+}
 
 // ---------------------------------------------------------------- Philox4x32-10
 // Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",

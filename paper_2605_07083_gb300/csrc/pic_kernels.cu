@@ -974,6 +974,12 @@ __global__ void __launch_bounds__(kPostThreads) k_post(DevState st) {
   }
   __syncthreads();
   field_solve(ic, rho_s, st.E + ic.node_off, st.phi + ic.node_off, ws64);
+  if (profile_due(st.prof_period, ic.window_start, step)) {
+    double* ps = st.phi_sum + ic.node_off;
+    const double* ph = st.phi + ic.node_off;
+    for (int j = tid; j < nn; j += nt) ps[j] += ph[j];
+    if (tid == 0) st.prof_n[inst] += 1;
+  }
 
   // ---- F: counts, ids, window, step
   if (tid == 0) {
@@ -995,6 +1001,42 @@ __global__ void __launch_bounds__(kPostThreads) k_post(DevState st) {
     dyn->ev_count = 0;
     dyn->step = step + 1;
   }
+}
+
+// ------------------------------------------------------------------ profiles
+// Species density samples for the Sec. 3 late-time profiles: after a sampled
+// step every particle of a species is binned with the charge's linear-weight
+// rule (2^24 units per particle, no sign or weight) into a block histogram,
+// which is added to the species' sums.  Grid (x, segment): the x blocks of a
+// segment stride over its particles; the launch sizes x so that no block sees
+// more than 2^20 particles (the 32-bit counters' bound).  Steps that are not
+// samples return at once.
+__global__ void __launch_bounds__(256) k_profile(DevState st) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int g = blockIdx.y;
+  const int inst = g / 3, sp = g - 3 * inst;
+  const InstConst& ic = st.ic[inst];
+  if (!profile_due(st.prof_period, ic.window_start, st.dyn[inst].step - 1)) return;
+  const int Nz = ic.Nz;
+  unsigned* hb = reinterpret_cast<unsigned*>(smem);
+  const Hist h{hb, hb + Nz, hb + 2 * Nz};
+  hist_zero(h, Nz);
+  __syncthreads();
+  const int n = st.seg_count[g];
+  const float* zs = st.z + st.seg_off[g];
+  const float inv = ic.inv_dz_f;
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int i = base + threadIdx.x;
+    float zz[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    unsigned am = 0u;
+    if (i < n) {
+      zz[0] = zs[i];
+      am = 1u;
+    }
+    deposit_warp(h, zz, am, inv, Nz);
+  }
+  __syncthreads();
+  hist_flush(h, Nz, 1LL, st.prof + (long long)sp * st.tn + ic.node_off);
 }
 
 // ------------------------------------------------------------------ helpers

@@ -87,6 +87,12 @@ class PicProfile(C.Structure):
                 ("push_launches", C.c_int64)]
 
 
+class PicVC(C.Structure):
+    _fields_ = [("samples", C.c_int64), ("T_emit_eV", C.c_double),
+                ("net_efficiency", C.c_double), ("phi_vc_eff", C.c_double),
+                ("phi_min", C.c_double), ("z_min", C.c_double), ("eta_vc", C.c_double)]
+
+
 # every entry point declared in include/pic.h: name -> (restype, argtypes)
 _P = C.c_void_p
 ENTRY_POINTS = {
@@ -101,6 +107,12 @@ ENTRY_POINTS = {
     "pic_get_rho_fixed": (C.c_int, [_P, C.c_int, _P, C.c_int64]),
     "pic_get_field": (C.c_int, [_P, C.c_int, _P, _P, C.c_int64]),
     "pic_set_step": (C.c_int, [_P, C.c_int64]),
+    "pic_set_profile_period": (C.c_int, [_P, C.c_int64]),
+    "pic_get_profiles": (C.c_int, [_P, C.c_int, C.c_int64, _P, _P, _P, C.POINTER(C.c_int64)]),
+    "pic_virtual_cathode": (C.c_int, [_P, C.c_int, C.c_double, C.POINTER(PicVC)]),
+    "pic_checkpoint_bytes": (C.c_int, [_P, C.POINTER(C.c_size_t)]),
+    "pic_save": (C.c_int, [_P, _P, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "pic_load": (C.c_int, [_P, _P, C.c_size_t]),
     "pic_tune": (C.c_int, [_P, C.POINTER(PicTuning)]),
     "pic_sort": (C.c_int, [_P]),
     "pic_synchronize": (C.c_int, [_P]),
@@ -140,7 +152,7 @@ def load(path: str = LIB_PATH):
                 fn = getattr(lib, name)
                 fn.restype = res
                 fn.argtypes = args
-            for i, st in enumerate((PicConfig, PicTuning, PicDiag, PicProfile)):
+            for i, st in enumerate((PicConfig, PicTuning, PicDiag, PicProfile, PicVC)):
                 if lib.pic_sizeof(i) != C.sizeof(st):
                     raise ImportError("struct %s: C size %d != ctypes size %d"
                                       % (st.__name__, lib.pic_sizeof(i), C.sizeof(st)))
@@ -307,6 +319,44 @@ def pic_set_step(h, step):
     _check(load().pic_set_step(h, int(step)), "pic_set_step")
 
 
+def pic_set_profile_period(h, period):
+    _check(load().pic_set_profile_period(h, int(period)), "pic_set_profile_period")
+
+
+def pic_get_profiles(h, instance, n_nodes) -> dict:
+    phi = np.empty(n_nodes, np.float64)
+    dens = np.empty((3, n_nodes), np.float64)
+    cnt = np.empty((3, n_nodes), np.int64)
+    k = C.c_int64()
+    _check(load().pic_get_profiles(h, instance, n_nodes, phi.ctypes.data_as(C.c_void_p),
+                                   dens.ctypes.data_as(C.c_void_p),
+                                   cnt.ctypes.data_as(C.c_void_p), C.byref(k)),
+           "pic_get_profiles")
+    return {"phi": phi, "density": dens, "counts": cnt, "samples": k.value}
+
+
+def pic_virtual_cathode(h, instance=0, near_fraction=0.1) -> dict:
+    v = PicVC()
+    _check(load().pic_virtual_cathode(h, instance, float(near_fraction), C.byref(v)),
+           "pic_virtual_cathode")
+    return {n: getattr(v, n) for n, _ in PicVC._fields_}
+
+
+def pic_save(h) -> bytes:
+    lib = load()
+    n = C.c_size_t()
+    _check(lib.pic_checkpoint_bytes(h, C.byref(n)), "pic_checkpoint_bytes")
+    buf = C.create_string_buffer(n.value)
+    w = C.c_size_t()
+    _check(lib.pic_save(h, buf, n.value, C.byref(w)), "pic_save")
+    return buf.raw[:w.value]
+
+
+def pic_load(h, data: bytes):
+    buf = C.create_string_buffer(bytes(data), len(data))
+    _check(load().pic_load(h, buf, len(data)), "pic_load")
+
+
 def pic_tune(h, push_threads=0, push_blocks_per_sm=0, sort_period=0, graph_steps=0):
     t = PicTuning()
     t.size = C.sizeof(PicTuning)
@@ -394,6 +444,21 @@ class Diode:
 
     def tune(self, **kw):
         pic_tune(self._h, **kw)
+
+    def set_profile_period(self, period):
+        pic_set_profile_period(self._h, period)
+
+    def profiles(self, instance=0):
+        return pic_get_profiles(self._h, instance, self.nodes(instance))
+
+    def virtual_cathode(self, instance=0, near_fraction=0.1):
+        return pic_virtual_cathode(self._h, instance, near_fraction)
+
+    def save(self) -> bytes:
+        return pic_save(self._h)
+
+    def load(self, data: bytes):
+        pic_load(self._h, data)
 
     def sort(self):
         pic_sort(self._h)
