@@ -317,6 +317,53 @@ __device__ __forceinline__ unsigned push_one(const SegCtx& c, const float2* Es2,
   return 0u;
 }
 
+// Four particles of one lane, with no data-dependent branch: the gathers,
+// pushes and the four Philox2x32 chains are independent and interleave.  The
+// candidate word is computed for absorbed particles too and masked off.
+__device__ __forceinline__ void push_quad(const SegCtx& c, const float2* Es2, float4& z4,
+                                          float4& v4, const uint4& id4, unsigned& dm,
+                                          unsigned& cm) {
+  float z[4] = {z4.x, z4.y, z4.z, z4.w};
+  float v[4] = {v4.x, v4.y, v4.z, v4.w};
+  const uint32_t id[4] = {id4.x, id4.y, id4.z, id4.w};
+  unsigned d = 0u;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    int j;
+    float f;
+    cell_of(z[k], c.inv_dz, c.Nz, j, f);
+    const float2 e = Es2[j];
+    v[k] = fmaf(c.qmdt, fmaf(f, e.y, e.x), v[k]);
+    z[k] = fmaf(v[k], c.dt, z[k]);
+    d |= (z[k] >= 0.0f && z[k] < c.Lf) ? 0u : (1u << k);
+  }
+  unsigned m = 0u;
+  if (c.tc != 0u) {                      // uniform over the segment
+    uint32_t a[4], b[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      a[k] = id[k];
+      b[k] = c.stepw;
+    }
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const unsigned long long p = (unsigned long long)0xD256D193u * a[k];
+        a[k] = (uint32_t)(p >> 32) ^ c.rk[r] ^ b[k];
+        b[k] = (uint32_t)p;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) m |= (a[k] < c.tc) ? (1u << k) : 0u;
+    m &= ~d;
+  }
+  z4 = make_float4(z[0], z[1], z[2], z[3]);
+  v4 = make_float4(v[0], v[1], v[2], v[3]);
+  dm = d;
+  cm = m;
+}
+
 template <bool kDepositOnly>
 __device__ __forceinline__ void push_body(const DevState& st) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -469,13 +516,7 @@ __device__ __forceinline__ void push_body(const DevState& st) {
             am = 0xFu;
           } else {
             float4 v4 = v4s;
-            const uint4 id4 = id4s;
-            const unsigned r0 = push_one(c, Es2, z4.x, v4.x, id4.x);
-            const unsigned r1 = push_one(c, Es2, z4.y, v4.y, id4.y);
-            const unsigned r2 = push_one(c, Es2, z4.z, v4.z, id4.z);
-            const unsigned r3 = push_one(c, Es2, z4.w, v4.w, id4.w);
-            dm = (r0 & 1u) | ((r1 & 1u) << 1) | ((r2 & 1u) << 2) | ((r3 & 1u) << 3);
-            cm = (r0 >> 1) | ((r1 >> 1) << 1) | ((r2 >> 1) << 2) | ((r3 >> 1) << 3);
+            push_quad(c, Es2, z4, v4, id4s, dm, cm);
             am = ~dm & 0xFu;
             __stcs(reinterpret_cast<float4*>(zp + i), z4);
             __stcs(reinterpret_cast<float4*>(vzp + i), v4);
