@@ -31,10 +31,16 @@ _DIAG_KEYS = ("gamma_emit", "gamma_emit_realized", "gamma_ref", "gamma_net", "ga
 
 def run(fluxes=W.TABLE2_FLUXES, ppc=1000, n_steps=4_500_000, window_start=None,
         profile_period=1000, chunk=50_000, max_seconds=None, seed=3, log=sys.stderr,
-        profile_points=512) -> dict:
-    """Run the scan; stop early (and say so) if max_seconds would be passed."""
+        profile_points=512, table3=False) -> dict:
+    """Run the scan (or, with table3, the Table 3 sensitivity cases) as one
+    batched job; stop early (and say so) if max_seconds would be passed."""
     import torch
-    ps = W.paper_flux_scan(fluxes, ppc=ppc, n_steps=n_steps, window_start=window_start, seed=seed)
+    if table3:
+        ps = W.paper_table3_cases(ppc=ppc, n_steps=n_steps, window_start=window_start)
+        fluxes = tuple(p["gamma_emit"] / 1e19 for p in ps)
+    else:
+        ps = W.paper_flux_scan(fluxes, ppc=ppc, n_steps=n_steps, window_start=window_start,
+                               seed=seed)
     d = pic.Diode(ps)
     for i, p in enumerate(ps):
         st = W.paper_initial_plasma(p, seed=1000 + i)
@@ -66,7 +72,8 @@ def run(fluxes=W.TABLE2_FLUXES, ppc=1000, n_steps=4_500_000, window_start=None,
     for i, p in enumerate(ps):
         dg = d.diagnostics(i, check=False)
         row = {"gamma_emit_1e19": p["gamma_emit"] / 1e19, "seed": p["seed"],
-               "n_live": dg["n_live"], "rc": dg["rc"]}
+               "label": p.get("label", ""), "ppc": p["ppc"], "n_live": dg["n_live"],
+               "rc": dg["rc"], "collisions": dg["collisions"].tolist()}
         row.update({k: dg[k] for k in _DIAG_KEYS})
         prof = d.profiles(i)
         if prof["samples"] > 0:
@@ -99,19 +106,22 @@ def main(argv=None):
     ap.add_argument("--max-seconds", type=float, default=None)
     ap.add_argument("--fluxes", type=str, default=None,
                     help="comma-separated fluxes in 1e19 m^-2 s^-1 (default: Table 2)")
+    ap.add_argument("--table3", action="store_true",
+                    help="run the Table 3 sensitivity cases instead of the flux scan")
     ap.add_argument("--out", type=str, default=None)
     a = ap.parse_args(argv)
     fl = tuple(float(x) for x in a.fluxes.split(",")) if a.fluxes else W.TABLE2_FLUXES
     res = run(fl, ppc=a.ppc, n_steps=a.steps, window_start=a.window_start,
-              profile_period=a.profile_period, chunk=a.chunk, max_seconds=a.max_seconds)
+              profile_period=a.profile_period, chunk=a.chunk, max_seconds=a.max_seconds,
+              table3=a.table3)
     txt = json.dumps(res)
     if a.out:
         with open(a.out, "w") as f:
             f.write(txt)
     print(json.dumps({k: v for k, v in res.items() if k != "rows"}))
     for r in res["rows"]:
-        print("%6.2f  backflow %.4f  net %.4f  anode %.4f  q_cool1 %.2f  phi_eff %s" % (
-            r["gamma_emit_1e19"], r["backflow_ratio"], r["net_efficiency"],
+        print("%-12s %6.2f  backflow %.4f  net %.4f  anode %.4f  q_cool1 %.2f  phi_eff %s" % (
+            r["label"], r["gamma_emit_1e19"], r["backflow_ratio"], r["net_efficiency"],
             r["collection_efficiency"], r["q_cooling_1"],
             "%.4f" % r["virtual_cathode"]["phi_vc_eff"] if "virtual_cathode" in r else "-"))
 
