@@ -288,10 +288,10 @@ int set_launch_shape(pic_handle* h) {
     h->st.dcount = (int32_t*)p;
     h->dcount_ints = need;
   }
-  // species phase: staged dead list + block starts + block prefix; tail:
-  // charge, two appended-particle histograms and the event keys
+  // compaction: staged dead list + block starts + block prefix; appends:
+  // the event keys; tail: the charge
   const size_t species = (size_t)kDeadSmem * 4 + (size_t)(h->G + 1) * 12 + 16;
-  const size_t tail = (size_t)h->max_nodes * 32 + 8 + (size_t)kEvCap * 8;
+  const size_t tail = std::max((size_t)kEvCap * 8, (size_t)h->max_nodes * 8 + 16);
   h->post_smem = std::max(species, tail);
   // profile sampler: blocks per segment so that none bins more than 2^20
   // particles (its 32-bit counters), else about two blocks per SM in total

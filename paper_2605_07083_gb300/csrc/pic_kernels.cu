@@ -738,55 +738,146 @@ __device__ __forceinline__ void block_reduce4(long long& c0, long long& c1, doub
   __syncthreads();
 }
 
-// Three blocks per diode, one per species: ordered absorbed list, boundary
-// tallies, deterministic hole filling.  The last of the three to finish
-// (an arrival counter; nothing waits) appends the step's new particles,
-// deposits them and solves the field.
-__global__ void __launch_bounds__(kPostThreads) k_post(DevState st) {
+// Linear-weight deposit of one particle per lane straight into the global
+// fixed-point charge (used for the few particles appended per step).  Lanes
+// in the cell of the warp's first active lane add their units in registers
+// first (32 x 2^24 < 2^32): the emitted electrons of a step all sit in the
+// first cells.  Called by all 32 lanes.
+__device__ __forceinline__ void deposit_global(int64_t* rho, long long sgn, float z, bool act,
+                                               float inv_dz, int Nz) {
+  int j = 0;
+  unsigned q = 0u;
+  if (act) {
+    float f;
+    cell_of(z, inv_dz, Nz, j, f);
+    q = (unsigned)frac_units(f);
+  }
+  const unsigned am = __ballot_sync(0xffffffffu, act);
+  if (am == 0u) return;
+  const int lead = __ffs(am) - 1;
+  const int j0 = __shfl_sync(0xffffffffu, j, lead);
+  const bool same = act && j == j0;
+  const unsigned sm = __ballot_sync(0xffffffffu, same);
+  const unsigned qs = __reduce_add_sync(0xffffffffu, same ? q : 0u);
+  unsigned long long* r = reinterpret_cast<unsigned long long*>(rho);
+  if ((int)(threadIdx.x & 31) == lead) {
+    atomicAdd(r + j0, (unsigned long long)(sgn * ((long long)__popc(sm) * kTwo24 - (long long)qs)));
+    atomicAdd(r + j0 + 1, (unsigned long long)(sgn * (long long)qs));
+  }
+  if (act && !same) {
+    atomicAdd(r + j, (unsigned long long)(sgn * ((long long)kTwo24 - (long long)q)));
+    atomicAdd(r + j + 1, (unsigned long long)(sgn * (long long)q));
+  }
+}
+
+// Ionisation events of the step ordered by parent id: keys (parent << 32 | k)
+// in evk[0, P2), bitonic sort in shared memory.
+__device__ void sort_events(const Event* evb, int E, unsigned long long* evk) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (E <= 1) {
+    if (E == 1 && tid == 0) evk[0] = 0ull;
+    __syncthreads();
+    return;
+  }
+  int P2 = 1;
+  while (P2 < E) P2 <<= 1;
+  for (int k = tid; k < P2; k += nt)
+    evk[k] = (k < E) ? (((unsigned long long)evb[k].parent << 32) | (unsigned)k) : ~0ull;
+  __syncthreads();
+  for (int kk = 2; kk <= P2; kk <<= 1) {
+    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+      for (int i = tid; i < P2; i += nt) {
+        const int ixj = i ^ jj;
+        if (ixj > i) {
+          const unsigned long long a = evk[i], b = evk[ixj];
+          const bool up = (i & kk) == 0;
+          if ((a > b) == up) { evk[i] = b; evk[ixj] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Three blocks per diode, one per species.  Each compacts its species
+// (ordered absorbed list, boundary tallies, deterministic hole filling) and
+// appends the species' new particles of the step -- thermionic electrons
+// (species 0), ionisation children and replenished pairs (species 1 and 2)
+// -- depositing them into the fixed-point charge.  The particle ids of all
+// appends follow from counts every block can compute (events, emission count,
+// ions absorbed), so the blocks need nothing from one another.  The last of
+// the three to finish (an arrival counter; nothing waits) solves the field
+// and closes the diode's step.
+__global__ void __launch_bounds__(kPostThreads, 1) k_post(DevState st) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int mn = st.max_nodes;
   __shared__ long long wsl[64];
   __shared__ double wsd2[64];
   __shared__ long long ws64[32];
   __shared__ int ws32[32];
   __shared__ InstConst ic;
-  __shared__ int sD[3], sN[3], sNn[3];
+  __shared__ int sE, sNemit, sLast;
   __shared__ long long sCnt[3][2];
   __shared__ double sKe[3][2];
-  __shared__ int sNemit, sE, sLast;
+  __shared__ int sN[3], sD[3];
 
-  const int inst = blockIdx.x / 3, my_sp = blockIdx.x - 3 * inst;
+  const int inst = blockIdx.x / 3, sp = blockIdx.x - 3 * inst;
   const int tid = threadIdx.x, nt = blockDim.x;
   {
     const int* src = reinterpret_cast<const int*>(st.ic + inst);
     int* dst = reinterpret_cast<int*>(&ic);
     for (int w = tid; w < (int)(sizeof(InstConst) / 4); w += nt) dst[w] = src[w];
   }
+  __syncthreads();                 // ic is read by every thread below
   InstDyn* dyn = st.dyn + inst;
   PostScratch* ps = st.post + inst;
   const long long Q = st.part[st.n_seg];
   const int Geff = (int)st.part[st.n_seg + 1];
+  const long long step = dyn->step;
+  const uint32_t base_id = dyn->next_id;
+  if (tid == 0) {
+    int e = dyn->ev_count;
+    if (e > kEvCap) {
+      atomicOr(&dyn->err, ERR_CAPACITY);
+      e = kEvCap;
+    }
+    sE = e;
+    long long nem = ic.emit_floor;
+    if (ic.t_frac != 0u) {
+      const uint4 r = philox10(make_uint4(0u, (uint32_t)step, 0u, TAG_EMIT_N), ic.key0[kStreamInject], ic.key1);
+      if (r.x < ic.t_frac) nem += 1;
+    }
+    sNemit = (int)nem;
+  }
 
-  // ---- species phase
+  // ---- compaction of this species
+  const int g = inst * 3 + sp;
+  const long long off = st.seg_off[g];
+  const int N = st.seg_count[g];
+  const int cap = st.seg_cap[g];
+  int D, Nn, P;
+  long long cnt0 = 0, cnt1 = 0;
+  double ke0 = 0.0, ke1 = 0.0;
   {
     uint32_t* dd_s = reinterpret_cast<uint32_t*>(smem);                 // kDeadSmem slots
     long long* blo = reinterpret_cast<long long*>(dd_s + kDeadSmem);    // [Geff + 1]
     int* bpre = reinterpret_cast<int*>(blo + Geff + 1);                 // [Geff + 1]
-    const int sp = my_sp;
-    const int g = inst * 3 + sp;
-    const long long off = st.seg_off[g];
-    const int N = st.seg_count[g];
     const long long qg = (N + 3) >> 2;
     const long long Sg = st.part[g];
+    // the ions' quad range, for the replenishment count of the electron block
+    const int gi = inst * 3 + 2;
+    const long long Si = st.part[gi], qi = st.part[gi + 1] - Si;
+    const bool need_ions = ic.replenish && sp == 1;
     for (int b = tid; b <= Geff; b += nt) blo[b] = (long long)b * Q / Geff;
     __syncthreads();
-    int carry = 0;
+    int carry = 0, ions = 0;
     for (int base = 0; base < Geff; base += nt) {
       const int b = base + tid;
       int c = 0;
-      if (b < Geff && qg > 0) {
+      if (b < Geff) {
         const long long lb = blo[b], hb = blo[b + 1];
-        if (lb < hb && lb < Sg + qg && hb > Sg) c = st.dcount[(long long)g * st.G + b];
+        if (qg > 0 && lb < hb && lb < Sg + qg && hb > Sg) c = st.dcount[(long long)g * st.G + b];
+        if (need_ions && qi > 0 && lb < hb && lb < Si + qi && hb > Si)
+          ions += st.dcount[(long long)gi * st.G + b];
       }
       int tot;
       const int ex = block_exclusive_scan<int>(c, &tot, ws32);
@@ -794,11 +885,10 @@ __global__ void __launch_bounds__(kPostThreads) k_post(DevState st) {
       carry += tot;
     }
     if (tid == 0) bpre[Geff] = carry;
+    if (need_ions) ions = block_sum<int>(ions, ws32);
     __syncthreads();
-    const int D = carry;
+    D = carry;
     uint32_t* dd = (D <= kDeadSmem) ? dd_s : st.dead_buf + off;
-    long long cnt0 = 0, cnt1 = 0;
-    double ke0 = 0.0, ke1 = 0.0;
     const double mw = 0.5 * ic.m_d[sp] * ic.weight;
     for (int k = tid; k < D; k += nt) {
       int blo_i = 0, bhi_i = Geff;
@@ -816,8 +906,9 @@ __global__ void __launch_bounds__(kPostThreads) k_post(DevState st) {
       if (z < 0.0f) { cnt0 += 1; ke0 += ke; } else { cnt1 += 1; ke1 += ke; }
     }
     block_reduce4(cnt0, cnt1, ke0, ke1, wsl, wsd2);   // also orders dd writes
-    // hole filling
-    const int Nn = N - D;
+    // hole filling: the dead slots below the new count take the live
+    // particles above it, in order
+    Nn = N - D;
     int lo = 0, hi = D;
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
@@ -842,37 +933,129 @@ __global__ void __launch_bounds__(kPostThreads) k_post(DevState st) {
       if (live) move_particle(st, off, t, dd[r]);
       run += tot;
     }
-    // every thread's moves are complete and visible before the arrival: the
-    // tail appends into the slots the hole filling read from
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) {
-      ps->D[sp] = D;
-      ps->N[sp] = N;
-      ps->Nn[sp] = Nn;
-      ps->cnt[sp][0] = cnt0;
-      ps->cnt[sp][1] = cnt1;
-      ps->ke[sp][0] = ke0;
-      ps->ke[sp][1] = ke1;
-      __threadfence();
-      sLast = (atomicAdd(&ps->arrive, 1u) == 2u);
-    }
-    __syncthreads();
-    if (!sLast) return;
+    P = !ic.replenish ? 0 : (sp == 2 ? D : (sp == 1 ? ions : 0));
+    __syncthreads();                 // shared memory is reused below
   }
+
+  // ---- appends of this species and their charge
+  const int E = sE, Nemit = sNemit;
+  const uint32_t id_emit = base_id + 2u * (uint32_t)E;
+  const uint32_t id_repl = id_emit + (uint32_t)Nemit;
+  int64_t* rho = st.rho_acc + ic.node_off;
+  bool overflow = false;
+  int newN = Nn;
+  if (sp == 0) {
+    // thermionic electrons (Sec. 2.2): flux-weighted half-Maxwellian, z = v_z dt
+    for (int base = 0; base < Nemit; base += nt) {
+      const int k = base + tid;
+      bool act = false;
+      float z = 0.0f;
+      if (k < Nemit) {
+        const uint4 r = philox10(make_uint4((uint32_t)k, (uint32_t)step, 0u, TAG_EMIT),
+                                 ic.key0[kStreamInject], ic.key1);
+        float n0, n1;
+        box_muller(r.x, r.y, n0, n1);
+        const float vz = ic.sig_w * sqrtf(-2.0f * logf(u01f(r.z)));
+        z = vz * ic.dt_f;
+        const long long sl = (long long)Nn + k;
+        if (sl < cap) {
+          put_particle(st, off, sl, z, ic.sig_w * n0, ic.sig_w * n1, vz, id_emit + (uint32_t)k);
+          act = true;
+        } else {
+          overflow = true;
+        }
+      }
+      deposit_global(rho, -1LL, z, act, ic.inv_dz_f, ic.Nz);
+    }
+    newN = min(Nn + Nemit, cap);
+  } else {
+    const long long sgn = (sp == 2) ? 1LL : -1LL;
+    const uint32_t idb = (sp == 2) ? 1u : 0u;
+    // ionisation children (Sec. 2.2 reading): the electron as a plasma
+    // electron, the ion at the neutral's velocity, ordered by parent id
+    unsigned long long* evk = reinterpret_cast<unsigned long long*>(smem);
+    const Event* evb = st.ev_buf + (long long)inst * kEvCap;
+    sort_events(evb, E, evk);
+    for (int base = 0; base < E; base += nt) {
+      const int k = base + tid;
+      bool act = false;
+      float z = 0.0f;
+      if (k < E) {
+        const Event ev = evb[(int)(evk[k] & 0xffffffffu)];
+        z = ev.z;
+        const long long sl = (long long)Nn + k;
+        if (sl < cap) {
+          const bool ion = sp == 2;
+          put_particle(st, off, sl, z, ion ? ev.vi[0] : ev.ve[0], ion ? ev.vi[1] : ev.ve[1],
+                       ion ? ev.vi[2] : ev.ve[2], base_id + 2u * k + idb);
+          act = true;
+        } else {
+          overflow = true;
+        }
+      }
+      deposit_global(rho, sgn, z, act, ic.inv_dz_f, ic.Nz);
+    }
+    // replenishment (Sec. 2.1): one e-ion pair at a common uniform position
+    // per ion absorbed; both blocks draw the pair's numbers
+    const float sig = (sp == 2) ? ic.sig_i0 : ic.sig_e0;
+    for (int base = 0; base < P; base += nt) {
+      const int k = base + tid;
+      bool act = false;
+      float z = 0.0f;
+      if (k < P) {
+        const uint4 A = philox10(make_uint4((uint32_t)k, (uint32_t)step, 0u, TAG_REPL), ic.key0[kStreamInject], ic.key1);
+        const uint4 B = philox10(make_uint4((uint32_t)k, (uint32_t)step, 1u, TAG_REPL), ic.key0[kStreamInject], ic.key1);
+        float gg[6];
+        box_muller(A.x, A.y, gg[0], gg[1]);
+        box_muller(A.z, A.w, gg[2], gg[3]);
+        box_muller(B.x, B.y, gg[4], gg[5]);
+        z = u01f(B.z) * ic.L_f;
+        const long long sl = (long long)Nn + E + k;
+        if (sl < cap) {
+          const bool ion = sp == 2;
+          put_particle(st, off, sl, z, sig * (ion ? gg[3] : gg[0]), sig * (ion ? gg[4] : gg[1]),
+                       sig * (ion ? gg[5] : gg[2]), id_repl + 2u * k + idb);
+          act = true;
+        } else {
+          overflow = true;
+        }
+      }
+      deposit_global(rho, sgn, z, act, ic.inv_dz_f, ic.Nz);
+    }
+    newN = min(Nn + E + P, cap);
+  }
+  if (__syncthreads_or(overflow) && tid == 0) atomicOr(&dyn->err, ERR_CAPACITY);
+
+  // every thread's moves, appends and charge are complete and visible before
+  // the arrival
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    st.seg_count[g] = newN;
+    ps->D[sp] = D;
+    ps->N[sp] = N;
+    ps->Nn[sp] = Nn;
+    ps->cnt[sp][0] = cnt0;
+    ps->cnt[sp][1] = cnt1;
+    ps->ke[sp][0] = ke0;
+    ps->ke[sp][1] = ke1;
+    __threadfence();
+    sLast = (atomicAdd(&ps->arrive, 1u) == 2u);
+  }
+  __syncthreads();
+  if (!sLast) return;
 
   // ---- tail: the last species block of this diode
   __threadfence();
   if (tid == 0) {
     const volatile PostScratch* vp = ps;
-    for (int sp = 0; sp < 3; ++sp) {
-      sD[sp] = vp->D[sp];
-      sN[sp] = vp->N[sp];
-      sNn[sp] = vp->Nn[sp];
-      sCnt[sp][0] = vp->cnt[sp][0];
-      sCnt[sp][1] = vp->cnt[sp][1];
-      sKe[sp][0] = vp->ke[sp][0];
-      sKe[sp][1] = vp->ke[sp][1];
+    for (int k = 0; k < 3; ++k) {
+      sD[k] = vp->D[k];
+      sN[k] = vp->N[k];
+      sCnt[k][0] = vp->cnt[k][0];
+      sCnt[k][1] = vp->cnt[k][1];
+      sKe[k][0] = vp->ke[k][0];
+      sKe[k][1] = vp->ke[k][1];
     }
     ps->arrive = 0u;
     if (inst == 0) {
@@ -881,162 +1064,37 @@ __global__ void __launch_bounds__(kPostThreads) k_post(DevState st) {
     }
   }
   __syncthreads();
+  // charge of the new state and its field
   long long* rho_s = reinterpret_cast<long long*>(smem);
-  Hist He, Hi;                                   // appended electrons / ions
-  He.cnt = reinterpret_cast<unsigned*>(smem + (size_t)mn * 8);
-  He.qh = He.cnt + mn;
-  He.ql = He.qh + mn;
-  Hi.cnt = He.ql + mn;
-  Hi.qh = Hi.cnt + mn;
-  Hi.ql = Hi.qh + mn;
-  unsigned long long* evk =
-      reinterpret_cast<unsigned long long*>(smem + (size_t)mn * 32 + ((mn & 1) ? 8 : 0));
-  const long long step = dyn->step;
-
-  // ---- C: ionisation events ordered by parent id
-  if (tid == 0) {
-    int e = dyn->ev_count;
-    if (e > kEvCap) {
-      atomicOr(&dyn->err, ERR_CAPACITY);
-      e = kEvCap;
-    }
-    sE = e;
-    long long nem = ic.emit_floor;
-    if (ic.t_frac != 0u) {
-      const uint4 r = philox10(make_uint4(0u, (uint32_t)step, 0u, TAG_EMIT_N), ic.key0[kStreamInject], ic.key1);
-      if (r.x < ic.t_frac) nem += 1;
-    }
-    sNemit = (int)nem;
-  }
-  __syncthreads();
-  const int E = sE;
-  const Event* evb = st.ev_buf + (long long)inst * kEvCap;
-  if (E > 1) {
-    int P2 = 1;
-    while (P2 < E) P2 <<= 1;
-    for (int k = tid; k < P2; k += nt)
-      evk[k] = (k < E) ? (((unsigned long long)evb[k].parent << 32) | (unsigned)k) : ~0ull;
-    __syncthreads();
-    for (int kk = 2; kk <= P2; kk <<= 1) {
-      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-        for (int i = tid; i < P2; i += nt) {
-          const int ixj = i ^ jj;
-          if (ixj > i) {
-            const unsigned long long a = evk[i], b = evk[ixj];
-            const bool up = (i & kk) == 0;
-            if ((a > b) == up) { evk[i] = b; evk[ixj] = a; }
-          }
-        }
-        __syncthreads();
-      }
-    }
-  } else if (E == 1 && tid == 0) {
-    evk[0] = 0ull;
-  }
-
-  // ---- D: appends (children, emission, replenishment) and their deposit
   const int nn = ic.Nz + 1;
-  hist_zero(He, ic.Nz);
-  hist_zero(Hi, ic.Nz);
-  __syncthreads();
-  const uint32_t base_id = dyn->next_id;
-  const int Nemit = sNemit;
-  const int P = ic.replenish ? (int)(sCnt[2][0] + sCnt[2][1]) : 0;
-  const int g0 = inst * 3, g1 = g0 + 1, g2 = g0 + 2;
-  const long long off0 = st.seg_off[g0], off1 = st.seg_off[g1], off2 = st.seg_off[g2];
-  const int cap0 = st.seg_cap[g0], cap1 = st.seg_cap[g1], cap2 = st.seg_cap[g2];
-  const int Nn0 = sNn[0], Nn1 = sNn[1], Nn2 = sNn[2];
-  bool overflow = false;
-  for (int k = tid; k < E; k += nt) {
-    const Event ev = evb[(int)(evk[k] & 0xffffffffu)];
-    const long long s1 = (long long)Nn1 + k, s2 = (long long)Nn2 + k;
-    if (s1 < cap1) {
-      put_particle(st, off1, s1, ev.z, ev.ve[0], ev.ve[1], ev.ve[2], base_id + 2u * k);
-      hist_deposit(He, ev.z, ic.inv_dz_f, ic.Nz);
-    } else overflow = true;
-    if (s2 < cap2) {
-      put_particle(st, off2, s2, ev.z, ev.vi[0], ev.vi[1], ev.vi[2], base_id + 2u * k + 1u);
-      hist_deposit(Hi, ev.z, ic.inv_dz_f, ic.Nz);
-    } else overflow = true;
-  }
-  const uint32_t id_emit = base_id + 2u * (uint32_t)E;
-  // emitted electrons all start in the first cell: warp-aggregated deposit
-  for (int base = 0; base < Nemit; base += nt) {
-    const int k = base + tid;
-    float zz[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    unsigned am = 0u;
-    if (k < Nemit) {
-      const uint4 r = philox10(make_uint4((uint32_t)k, (uint32_t)step, 0u, TAG_EMIT),
-                               ic.key0[kStreamInject], ic.key1);
-      float n0, n1;
-      box_muller(r.x, r.y, n0, n1);
-      const float vz = ic.sig_w * sqrtf(-2.0f * logf(u01f(r.z)));
-      const float z = vz * ic.dt_f;
-      const long long s = (long long)Nn0 + k;
-      if (s < cap0) {
-        put_particle(st, off0, s, z, ic.sig_w * n0, ic.sig_w * n1, vz, id_emit + (uint32_t)k);
-        zz[0] = z;
-        am = 1u;
-      } else {
-        overflow = true;
-      }
-    }
-    deposit_warp(He, zz, am, ic.inv_dz_f, ic.Nz);
-  }
-  const uint32_t id_repl = id_emit + (uint32_t)Nemit;
-  for (int k = tid; k < P; k += nt) {
-    const uint4 A = philox10(make_uint4((uint32_t)k, (uint32_t)step, 0u, TAG_REPL), ic.key0[kStreamInject], ic.key1);
-    const uint4 B = philox10(make_uint4((uint32_t)k, (uint32_t)step, 1u, TAG_REPL), ic.key0[kStreamInject], ic.key1);
-    float gg[6];
-    box_muller(A.x, A.y, gg[0], gg[1]);
-    box_muller(A.z, A.w, gg[2], gg[3]);
-    box_muller(B.x, B.y, gg[4], gg[5]);
-    const float z = u01f(B.z) * ic.L_f;
-    const long long s1 = (long long)Nn1 + E + k, s2 = (long long)Nn2 + E + k;
-    if (s1 < cap1) {
-      put_particle(st, off1, s1, z, ic.sig_e0 * gg[0], ic.sig_e0 * gg[1], ic.sig_e0 * gg[2],
-                   id_repl + 2u * k);
-      hist_deposit(He, z, ic.inv_dz_f, ic.Nz);
-    } else overflow = true;
-    if (s2 < cap2) {
-      put_particle(st, off2, s2, z, ic.sig_i0 * gg[3], ic.sig_i0 * gg[4], ic.sig_i0 * gg[5],
-                   id_repl + 2u * k + 1u);
-      hist_deposit(Hi, z, ic.inv_dz_f, ic.Nz);
-    } else overflow = true;
-  }
-  if (__syncthreads_or(overflow) && tid == 0) atomicOr(&dyn->err, ERR_CAPACITY);
-
-  // ---- E: charge of the new state and its field
   for (int j = tid; j < nn; j += nt) {
-    const long long v = st.rho_acc[ic.node_off + j] - hist_node(He, j, ic.Nz) + hist_node(Hi, j, ic.Nz);
+    const long long v = ((volatile long long*)rho)[j];
     rho_s[j] = v;
     st.rho[ic.node_off + j] = v;
-    st.rho_acc[ic.node_off + j] = 0;
+    rho[j] = 0;
   }
   __syncthreads();
   field_solve(ic, rho_s, st.E + ic.node_off, st.phi + ic.node_off, ws64);
   if (profile_due(st.prof_period, ic.window_start, step)) {
-    double* ps = st.phi_sum + ic.node_off;
+    double* pa = st.phi_sum + ic.node_off;
     const double* ph = st.phi + ic.node_off;
-    for (int j = tid; j < nn; j += nt) ps[j] += ph[j];
+    for (int j = tid; j < nn; j += nt) pa[j] += ph[j];
     if (tid == 0) st.prof_n[inst] += 1;
   }
 
-  // ---- F: counts, ids, window, step
+  // window tallies, ids, step
   if (tid == 0) {
-    st.seg_count[g0] = min(Nn0 + Nemit, cap0);
-    st.seg_count[g1] = min(Nn1 + E + P, cap1);
-    st.seg_count[g2] = min(Nn2 + E + P, cap2);
-    dyn->next_id = id_repl + 2u * (uint32_t)P;
+    const int Pt = ic.replenish ? sD[2] : 0;
+    dyn->next_id = id_repl + 2u * (uint32_t)Pt;
     if (step >= ic.window_start) {
       dyn->win_steps += 1;
-      for (int sp = 0; sp < 3; ++sp)
+      for (int k = 0; k < 3; ++k)
         for (int w = 0; w < 2; ++w) {
-          dyn->count[sp][w] += sCnt[sp][w];
-          dyn->ke[sp][w] += sKe[sp][w];
+          dyn->count[k][w] += sCnt[k][w];
+          dyn->ke[k][w] += sKe[k][w];
         }
       dyn->emitted += Nemit;
-      dyn->replenished += P;
+      dyn->replenished += Pt;
     }
     dyn->pushed += (long long)sN[0] + sN[1] + sN[2];
     dyn->ev_count = 0;

@@ -264,3 +264,33 @@ def test_periodic_sort_leaves_the_physics_bit_identical(env):
             assert np.array_equal(a[k], b[k]), k
     assert np.array_equal(d0["count"], d1["count"])
     np.testing.assert_allclose(d0["ke"], d1["ke"], rtol=1e-12)
+
+
+def test_production_determinism_over_many_steps(env):
+    """The 2048-cell production diode (a 2.6M-particle preload of the same
+    recipe): two runs give identical fixed-point charge at steps 1, 100 and
+    2000 and identical states and tallies."""
+    pic, O = env
+    p = W.single_diode_production(seed=9)
+    # ~750 electrons are emitted per step and few leave within 2000 steps
+    p["capacity"] = (4_000_000, 1_000_000, 1_000_000)
+    st = W.scaled_preload(p, seed=31, n_emit=2_000_000, n_pairs=300_000)
+    runs = []
+    for _ in range(2):
+        d = pic.Diode(p)
+        for sp in range(3):
+            d.inject(sp, *st[sp])
+        rhos = []
+        for n in (1, 99, 1900):
+            d.step(n)
+            rhos.append(d.rho_fixed())
+        runs.append((rhos, [by_id(d.state(sp)) for sp in range(3)], d.diagnostics()))
+        d.close()
+    (ra, sa, da), (rb, sb, db) = runs
+    for x, y in zip(ra, rb):
+        assert np.array_equal(x, y)
+    for x, y in zip(sa, sb):
+        for k in x:
+            assert np.array_equal(x[k], y[k])
+    assert np.array_equal(da["count"], db["count"]) and np.array_equal(da["ke"], db["ke"])
+    assert da["step"] == 2000 and da["emitted"] == db["emitted"]
