@@ -22,6 +22,7 @@ __global__ void k_mcc(DevState st);
 __global__ void k_post(DevState st);
 __global__ void k_field(DevState st);
 __global__ void k_profile(DevState st);
+__global__ void k_phi(DevState st);
 __global__ void k_fill_ids(uint32_t* id, long long n, uint32_t first);
 __global__ void k_count_outside(const float* z, long long n, float Lf, int* bad);
 void sort_launch(const DevState& st, int max_chunks, int max_nz, cudaStream_t s);
@@ -73,6 +74,7 @@ struct pic_handle {
   int graph_len = 0;
   size_t push_smem = 0, post_smem = 0, field_smem = 0;
   size_t dcount_ints = 0;
+  int bstart_len = 0;
   int mcc_blocks = 0;
   bool sort_ready = false;
   int sort_chunks = 1;
@@ -254,7 +256,7 @@ cudaError_t raise_smem_limits(int device) {
   cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   if (e != cudaSuccess) return e;
   const void* fns[] = {(const void*)k_push, (const void*)k_deposit, (const void*)k_field,
-                       (const void*)k_post, (const void*)k_profile};
+                       (const void*)k_post, (const void*)k_profile, (const void*)k_phi};
   for (const void* f : fns) {
     e = set_dynamic_smem_limit(f, optin);
     if (e != cudaSuccess) return e;
@@ -287,6 +289,12 @@ int set_launch_shape(pic_handle* h) {
     if (!p) return PIC_ENOMEM;
     h->st.dcount = (int32_t*)p;
     h->dcount_ints = need;
+  }
+  if (h->G + 1 > h->bstart_len) {
+    void* p = dev_alloc(h, sizeof(int64_t) * (size_t)(h->G + 1));
+    if (!p) return PIC_ENOMEM;
+    h->st.bstart = (int64_t*)p;
+    h->bstart_len = h->G + 1;
   }
   // compaction: staged dead list + block starts + block prefix; appends:
   // the event keys; tail: the charge
@@ -836,8 +844,11 @@ int pic_get_field(pic_handle* h, int instance, double* phi, float* E, int64_t n_
   int rc = ensure_field(h);
   if (rc != PIC_OK) return rc;
   const int off = h->ic[instance].node_off;
-  cudaError_t e = cudaSuccess;
-  if (phi) e = cudaMemcpyAsync(phi, h->st.phi + off, sizeof(double) * nn, cudaMemcpyDeviceToHost, h->stream);
+  // a step computes E only; phi of the current state is solved on request
+  k_phi<<<h->n_inst, kPostThreads, h->field_smem, h->stream>>>(h->st);
+  cudaError_t e = cudaGetLastError();
+  if (phi && e == cudaSuccess)
+    e = cudaMemcpyAsync(phi, h->st.phi + off, sizeof(double) * nn, cudaMemcpyDeviceToHost, h->stream);
   if (E && e == cudaSuccess)
     e = cudaMemcpyAsync(E, h->st.E + off, sizeof(float) * nn, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

@@ -108,6 +108,7 @@ struct DevState {
   const int32_t* seg_cap;  // [n_seg]
   int32_t* seg_count;      // [n_seg] live particles
   int64_t* part;           // [n_seg + 2]: quad prefix of the last push, Q, G_eff
+  int64_t* bstart;         // [G + 1]: first quad of each push block (b Q / G_eff)
   int32_t* dcount;         // [n_seg * G] absorbed particles per (segment, block)
   uint32_t* dead_buf;      // [total_cap] per-warp absorbed-slot lists (push), staging (post)
   uint32_t* dead_dense;    // [total_cap] per-block ordered absorbed-slot lists
@@ -220,20 +221,26 @@ __device__ __forceinline__ void iso_dir(uint32_t rc, uint32_t rp, float& dx, flo
 // Fixed-point cell rule, all FP32 round-to-nearest with no contraction:
 // s = z * inv_dz, j = floor(s) clamped to [0, Nz-1], f = s - j.
 // floor without a conversion: for 0 <= s < 2^22, s + 1.5*2^23 rounded toward
-// zero is 1.5*2^23 + floor(s) (unit spacing there), read from its bits.  A
-// negative or NaN s (never a live particle) maps to a huge unsigned value
-// and is clamped to the last cell, so every index stays in bounds.
+// zero is 1.5*2^23 + floor(s) (unit spacing there), read from its bits; the
+// same sum less 1.5*2^23 is floor(s) as a float, exactly, so f needs no
+// int-to-float conversion either.  A negative or NaN s (never a live
+// particle) maps to a huge unsigned value and is clamped to the last cell, so
+// every index stays in bounds.
 __device__ __forceinline__ void cell_of(float z, float inv_dz, int Nz, int& j, float& f) {
   const float s = __fmul_rn(z, inv_dz);
   const float t = __fadd_rz(s, 12582912.0f);
   unsigned jj = (unsigned)(__float_as_int(t) - 0x4B400000);
   jj = min(jj, (unsigned)(Nz - 1));
   j = (int)jj;
-  f = __fsub_rn(s, __int2float_rn((int)jj));
+  const float jf = fminf(__fsub_rn(t, 12582912.0f), (float)(Nz - 1));
+  f = __fsub_rn(s, jf);
 }
 
-__device__ __forceinline__ long long frac_units(float f) {
-  return (long long)__fmul_rn(f, 16777216.0f);
+// Q = trunc(f 2^24): f in [0, 1] makes the product exact and below 2^32, so a
+// 32-bit conversion gives the rule's value (a 64-bit one would run on the
+// FP64 pipe, which is narrow on this part).
+__device__ __forceinline__ unsigned frac_units(float f) {
+  return __float2uint_rz(__fmul_rn(f, 16777216.0f));
 }
 
 // ---------------------------------------------------------------- bulk copies

@@ -398,6 +398,12 @@ __device__ __forceinline__ void push_body(const DevState& st) {
   if ((int)blockIdx.x >= Geff) return;
   const long long lo = (long long)blockIdx.x * Q / Geff;
   const long long hi = ((long long)blockIdx.x + 1) * Q / Geff;
+  if (!kDepositOnly && threadIdx.x == 0) {
+    // the block ranges, for the post kernel (which would otherwise redo
+    // G_eff 64-bit divisions on one SM)
+    st.bstart[blockIdx.x] = lo;
+    if ((int)blockIdx.x == Geff - 1) st.bstart[Geff] = hi;
+  }
   if (lo >= hi) return;
   const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -609,8 +615,10 @@ __global__ void k_deposit(DevState st) { push_body<true>(st); }
 // summation: with d_j = phi_{j+1} - phi_j the difference equations give
 // d_j = d_0 - kappa G_j, G_j = sum_{k=1..j} rho_k (exact int64), and
 // phi_Nz = V fixes d_0 = (V + kappa sum_{j<Nz} G_j) / Nz.  E_j = -(d_j +
-// d_{j-1}) / (2 dz) inside, one-sided at the electrodes.  rho_s is the
-// block's shared copy of the fixed-point charge; it is overwritten with G.
+// d_{j-1}) / (2 dz) inside, one-sided at the electrodes.  phi_j = j d_0 -
+// kappa sum_{k<j} G_k is written only when phi is non-null: the push needs E
+// alone, and FP64 work is scarce on this part.  rho_s is the block's shared
+// copy of the fixed-point charge; it is overwritten with G.
 __device__ void field_solve(const InstConst& ic, long long* rho_s, float* E, double* phi,
                             long long* ws) {
   const int Nz = ic.Nz;
@@ -643,7 +651,9 @@ __device__ void field_solve(const InstConst& ic, long long* rho_s, float* E, dou
     }
   }
   long long Htot;
-  const long long hex = block_exclusive_scan<long long>(lsum, &Htot, ws);
+  long long hex = 0;
+  if (phi) hex = block_exclusive_scan<long long>(lsum, &Htot, ws);
+  else Htot = block_sum<long long>(lsum, ws);
 #pragma unroll
   for (int u = 0; u < 8; ++u)
     if (u < c && j0 + u < Nz) rho_s[j0 + u] = a[u];
@@ -658,12 +668,12 @@ __device__ void field_solve(const InstConst& ic, long long* rho_s, float* E, dou
     if (u < c && j < Nz) {
       const long long gsum = (j == 0) ? 0LL : a[u] + rho_s[j - 1];
       E[j] = (float)fma(B, (double)gsum, A);
-      phi[j] = fma((double)j, d0, -kap * (double)(hex + hx[u]));
+      if (phi) phi[j] = fma((double)j, d0, -kap * (double)(hex + hx[u]));
     }
   }
   if (threadIdx.x == 0) {
     E[Nz] = (float)fma(2.0 * B, (double)rho_s[Nz - 1], A);
-    phi[Nz] = ic.V;
+    if (phi) phi[Nz] = ic.V;
   }
   __syncthreads();
 }
@@ -681,6 +691,20 @@ __global__ void __launch_bounds__(kPostThreads) k_field(DevState st) {
     st.rho[off + j] = v;
     st.rho_acc[off + j] = 0;
   }
+  __syncthreads();
+  field_solve(ic, rho_s, st.E + off, st.phi + off, ws64);
+}
+
+// phi (and E, identically) of the current state from its fixed-point charge,
+// for callers that read the potential; a time step computes E only.
+__global__ void __launch_bounds__(kPostThreads) k_phi(DevState st) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  long long* rho_s = reinterpret_cast<long long*>(smem);
+  __shared__ long long ws64[32];
+  const InstConst& ic = st.ic[blockIdx.x];
+  const int nn = ic.Nz + 1;
+  const int off = ic.node_off;
+  for (int j = threadIdx.x; j < nn; j += blockDim.x) rho_s[j] = st.rho[off + j];
   __syncthreads();
   field_solve(ic, rho_s, st.E + off, st.phi + off, ws64);
 }
@@ -867,7 +891,7 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post(DevState st) {
     const int gi = inst * 3 + 2;
     const long long Si = st.part[gi], qi = st.part[gi + 1] - Si;
     const bool need_ions = ic.replenish && sp == 1;
-    for (int b = tid; b <= Geff; b += nt) blo[b] = (long long)b * Q / Geff;
+    for (int b = tid; b <= Geff; b += nt) blo[b] = st.bstart[b];
     __syncthreads();
     int carry = 0, ions = 0;
     for (int base = 0; base < Geff; base += nt) {
@@ -1074,8 +1098,9 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post(DevState st) {
     rho[j] = 0;
   }
   __syncthreads();
-  field_solve(ic, rho_s, st.E + ic.node_off, st.phi + ic.node_off, ws64);
-  if (profile_due(st.prof_period, ic.window_start, step)) {
+  const bool sample = profile_due(st.prof_period, ic.window_start, step);
+  field_solve(ic, rho_s, st.E + ic.node_off, sample ? st.phi + ic.node_off : nullptr, ws64);
+  if (sample) {
     double* pa = st.phi_sum + ic.node_off;
     const double* ph = st.phi + ic.node_off;
     for (int j = tid; j < nn; j += nt) pa[j] += ph[j];
