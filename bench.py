@@ -245,6 +245,7 @@ def run_ours(args, rank, world):
     achieved = ALG_BYTES_PER_PARTICLE * n_per_launch / (push_ms * 1e-3) / 1e9
     cpu = cpu_baseline(p, state) if not args.no_cpu else None
     batched = run_batched() if not args.no_batched else None
+    small = run_small() if not args.no_batched else None
     launches = 3 * args.steps
     out = {
         "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
@@ -268,6 +269,7 @@ def run_ours(args, rank, world):
                                                    "pic_diagnostics"},
         "gpu_launches": launches,
         "batched_sweep": batched,
+        "small_diode": small,
         "clocks": ck,
         "diag": {"n_live": diag["n_live"], "backflow_ratio": diag["backflow_ratio"],
                  "candidates": diag["candidates"].tolist()},
@@ -337,6 +339,32 @@ def run_batched(steps=100, warmup=20):
             "tuning": {k: tuning[k] for k in ("push_threads", "push_blocks_per_sm", "sort_period")},
             "workload": "64 He diodes: Gamma U[5,9]e19, gap U[1,5] mm (cells = gap/2.5 um), "
                         "n_He logU[1e21,1e22], 5e4-4e6 emitted e preloaded (log-uniform), 10 V"}
+
+
+def run_small(steps=2000):
+    """The 1 mm, 128-cell diode from an empty start (~2e4 emitted electrons
+    in flight once filled): launch-latency-bound and L2-resident, so it
+    carries no roofline claim."""
+    import torch
+    from paper_2605_07083_gb300 import pic
+    p = W.single_diode_small(seed=1)
+    d = pic.Diode(p)
+    d.step(50)
+    d.synchronize()
+    p0 = d.diagnostics()["particles_pushed"]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(d.stream)
+    d.step(steps)
+    e1.record(d.stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    dg = d.diagnostics()
+    d.close()
+    pushed = dg["particles_pushed"] - p0
+    return {"workload": "He diode 1 mm, 128 cells, dt 1e-12 s, 10 V, empty start, steps 50-2050",
+            "steps": steps, "ms_per_step": ms / steps, "value": pushed / (ms * 1e-3),
+            "unit": "particle-steps/s", "particles_final": int(sum(dg["n_live"])),
+            "note": "launch-latency-bound, L2-resident: no roofline claim"}
 
 
 def cpu_baseline(p, state, budget_s=12.0):
@@ -411,7 +439,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
-    ap.add_argument("--no-batched", action="store_true", help="skip the 64-diode sweep")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 64-diode sweep and the small-diode line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -179,6 +179,32 @@ def _bisect(settings, a, b, open_, est, cost, **kw):
                 open_[i] = False
 
 
+def _ksect(settings, a, b, open_, est, cost, k=3, **kw):
+    """Batched k-section of the crossing of 1/2 on the open settings: each
+    round evaluates k interior fluxes of every open bracket and keeps the
+    sub-interval where the backflow first reaches 1/2, so a bracket shrinks
+    (k + 1)-fold per round -- fewer rounds (GPU launches) than bisection for
+    k times the runs."""
+    while open_.any():
+        idx = np.nonzero(open_)[0]
+        pts = [a[i] + (b[i] - a[i]) * (j + 1) / (k + 1) for i in idx for j in range(k)]
+        bf = _eval([settings[i] for i in idx for _ in range(k)], pts, cost, **kw)
+        for m, i in enumerate(idx):
+            g = np.array(pts[m * k:(m + 1) * k])
+            v = bf[m * k:(m + 1) * k]
+            up = np.nonzero(v >= 0.5)[0]
+            if up.size:
+                j = int(up[0])
+                b[i] = g[j]
+                if j > 0:
+                    a[i] = g[j - 1]
+            else:
+                a[i] = g[-1]
+            if b[i] - a[i] <= 2 * TOL:
+                est[i] = 0.5 * (a[i] + b[i])
+                open_[i] = False
+
+
 def plain_search(settings, **kw):
     """Endpoints, then bisection to +-TOL.  est = nan: no crossing in range."""
     n = len(settings)
@@ -212,8 +238,8 @@ def guided_search(model, settings, max_err=0.02, **kw):
     +- TOL, or -- where it predicts none -- once, at the flux where its
     backflow is closest to 1/2.  A prediction stands when PIC confirms it
     (same side of 1/2 / bracket confirmed) and the surrogate is within
-    max_err of PIC at every evaluated flux; otherwise PIC bisection takes
-    over on what the evaluations leave."""
+    max_err of PIC at every evaluated flux; otherwise a PIC k-section (three
+    fluxes per bracket and round) takes over on what the evaluations leave."""
     n = len(settings)
     cost = {"gpu_ms": 0.0, "particle_steps": 0, "runs": 0, "rounds": 0}
     pred, bf_grid, grid = surrogate_crossing(model, settings)
@@ -273,7 +299,8 @@ def guided_search(model, settings, max_err=0.02, **kw):
         for k, i in enumerate(idx):
             if not (bfe[k] < 0.5 <= bfe[m + k]):
                 open_[i] = False                          # no crossing in range
-        _bisect(settings, a, b, open_, est, cost, **kw)
+        # the few fall-backs are searched in fewer, wider rounds
+        _ksect(settings, a, b, open_, est, cost, **kw)
     cost["fallback"] = int(fallback.sum())
     cost["surrogate_err_ok"] = float(np.mean(err_ok_all)) if n else 1.0
     cost["predicted_crossings"] = int(has.sum())

@@ -91,6 +91,20 @@ def test_one_step_matches_oracle(env, n_gas):
     p = W.single_diode_small()
     p.update(n_gas=n_gas, replenish=1, window_start=0)
     state = mixed_state(p, 13, 40000, 20000)
+    _check_one_step(env, p, state, n_gas > 1e22)
+
+
+def test_one_step_matches_oracle_on_the_paper_diode(env):
+    """The paper's 10 cm, 4096-cell, 40 V diode of the Table 2 scan (elastic +
+    CX, T_n,i = 1740 K, replenishment) at 7.25e19, from a mixed state."""
+    p = W.paper_flux_scan((7.25,), ppc=250)[0]
+    p["window_start"] = 0
+    p["n_gas"] = 3e23                      # many collisions in one step
+    state = mixed_state(p, 16, 100000, 200000)
+    _check_one_step(env, p, state, True)
+
+
+def _check_one_step(env, p, state, many_collisions):
     gpu, ora, ev, flips = _one_step_case(env, p, state)
     for sp in range(3):
         g, o = gpu.state(sp), ora.state(sp)
@@ -107,7 +121,7 @@ def test_one_step_matches_oracle(env, n_gas):
     assert np.abs(dg["count"] - to["count"]).sum() <= 2
     np.testing.assert_allclose(dg["ke"], to["ke"], rtol=1e-5, atol=1e-30)
     assert dg["emitted"] == to["emitted"] and dg["replenished"] == to["replenished"]
-    if n_gas > 1e22:
+    if many_collisions:
         assert dg["collisions"][1:].sum() > 100     # the case really exercises the MCC
 
 
