@@ -112,7 +112,13 @@ typedef struct pic_tuning {
     int32_t push_blocks_per_sm;  /* cap on resident blocks per SM (default: occupancy limit) */
     int32_t sort_period;      /* counting sort by cell every this many steps; < 0 disables */
     int32_t graph_steps;      /* steps captured per CUDA graph; < 0 disables graphs */
-    int32_t reserved[3];
+    int32_t wait_polls;       /* polls of a bulk-copy wait in the push kernel before it gives
+                                 up with PIC_ETIMEOUT (default 2^20, each suspending the warp
+                                 up to ~1 us): n > 0 sets n; -1 gives up without polling, a
+                                 way to exercise the time-out path (the kernel first lets its
+                                 copies in flight land, so nothing faults); -2 restores the
+                                 default */
+    int32_t reserved[2];
 } pic_tuning;
 
 /* Late-time diagnostics of one instance (Sec. 2.3, Eq. 1-8).  Fluxes in

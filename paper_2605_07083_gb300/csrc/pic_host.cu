@@ -549,6 +549,7 @@ int pic_create(const pic_config* cfgs, int n_instances, void* cuda_stream,
 
   DevState& st = h->st;
   st.n_inst = h->n_inst;
+  st.wait_limit = kWaitLimit;
   st.n_seg = h->n_seg;
   st.max_nodes = h->max_nodes;
   const size_t P = (size_t)h->total_cap;
@@ -1141,6 +1142,10 @@ int pic_tune(pic_handle* h, const pic_tuning* t) {
   }
   if (t->sort_period != 0) h->sort_period = t->sort_period < 0 ? 0 : t->sort_period;
   if (t->graph_steps != 0) h->graph_steps = t->graph_steps < 0 ? 0 : t->graph_steps;
+  if (t->wait_polls != 0) {
+    if (t->wait_polls < -2) return PIC_EINVAL;
+    h->st.wait_limit = t->wait_polls > 0 ? t->wait_polls : (t->wait_polls == -1 ? 0 : kWaitLimit);
+  }
   if (h->sort_period > 0) {
     int rc = sort_alloc(h);
     if (rc != PIC_OK) return rc;

@@ -131,6 +131,7 @@ struct DevState {
   double* phi_sum;         // [tn] sum of sampled phi
   int64_t* prof;           // [3][tn] sum of sampled species deposits, 2^24 units per particle
   int64_t* prof_n;         // [n_inst] samples taken
+  int wait_limit;          // polls of a push-kernel bulk-copy wait before PIC_ETIMEOUT
 };
 
 // Is the state after step n a profile sample?  (Sec. 3 late-time averages:
@@ -286,8 +287,9 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t 
   return ok != 0u;
 }
 // every wait ends: after kWaitLimit polls the caller gets false
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity) {
-  for (int it = 0; it < kWaitLimit; ++it)
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity,
+                                                  int limit = kWaitLimit) {
+  for (int it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }

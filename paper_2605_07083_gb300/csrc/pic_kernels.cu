@@ -497,11 +497,15 @@ __device__ __forceinline__ void push_body(const DevState& st) {
       uint4 id4s = make_uint4(0u, 0u, 0u, 0u);
       if (!kDepositOnly) {
         const int s = ch & 1;
-        const bool arrived = mbar_wait_bounded(&wbar[s], (phase >> s) & 1u);
+        const bool arrived = mbar_wait_bounded(&wbar[s], (phase >> s) & 1u, st.wait_limit);
         if (!__all_sync(0xffffffffu, arrived)) {
-          // the copy never completed: flag it, drain the other stage, stop
+          // the copy did not complete in time: flag it, let this warp's copies
+          // in flight (this stage and the next) land with the full limit, keep
+          // the stage parities in step, and stop this warp's part of the segment
           if (lane == 0) atomicOr(&st.dyn[inst].err, ERR_TIMEOUT);
-          if (ch + 1 < nchunks) mbar_wait_bounded(&wbar[s ^ 1], (phase >> (s ^ 1)) & 1u);
+          if (mbar_wait_bounded(&wbar[s], (phase >> s) & 1u)) phase ^= 1u << s;
+          if (ch + 1 < nchunks && mbar_wait_bounded(&wbar[s ^ 1], (phase >> (s ^ 1)) & 1u))
+            phase ^= 1u << (s ^ 1);
           break;
         }
         phase ^= 1u << s;

@@ -56,7 +56,8 @@ class PicAllocator(C.Structure):
 class PicTuning(C.Structure):
     _fields_ = [("size", C.c_uint32), ("push_threads", C.c_int32),
                 ("push_blocks_per_sm", C.c_int32), ("sort_period", C.c_int32),
-                ("graph_steps", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("graph_steps", C.c_int32), ("wait_polls", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
 _DIAG_DOUBLES = [
@@ -357,13 +358,15 @@ def pic_load(h, data: bytes):
     _check(load().pic_load(h, buf, len(data)), "pic_load")
 
 
-def pic_tune(h, push_threads=0, push_blocks_per_sm=0, sort_period=0, graph_steps=0):
+def pic_tune(h, push_threads=0, push_blocks_per_sm=0, sort_period=0, graph_steps=0,
+             wait_polls=0):
     t = PicTuning()
     t.size = C.sizeof(PicTuning)
     t.push_threads = push_threads
     t.push_blocks_per_sm = push_blocks_per_sm
     t.sort_period = sort_period
     t.graph_steps = graph_steps
+    t.wait_polls = wait_polls
     _check(load().pic_tune(h, C.byref(t)), "pic_tune")
 
 

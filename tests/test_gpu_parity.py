@@ -308,3 +308,48 @@ def test_production_determinism_over_many_steps(env):
             assert np.array_equal(x[k], y[k])
     assert np.array_equal(da["count"], db["count"]) and np.array_equal(da["ke"], db["ke"])
     assert da["step"] == 2000 and da["emitted"] == db["emitted"]
+
+
+def test_forced_wait_timeout_is_reported_and_the_context_stays_usable(env):
+    """A push kernel told to give up its bulk-copy waits at once reports
+    PIC_ETIMEOUT (after letting its copies in flight land); the device stays
+    usable and a fresh handle steps normally."""
+    pic, O = env
+    p = W.single_diode_small()
+    st = mixed_state(p, 17, 20001, 5001)
+    d = pic.Diode(p)
+    for sp in range(3):
+        d.inject(sp, *st[sp])
+    d.tune(wait_polls=-1)
+    d.step(3)
+    assert d.synchronize() == pic.PIC_ETIMEOUT
+    assert d.diagnostics(check=False)["error_flags"] & (1 << 4)
+    with pytest.raises(pic.PicError):
+        d.step(1)                          # the error is sticky
+    d.close()
+    fresh = pic.Diode(p)
+    for sp in range(3):
+        fresh.inject(sp, *st[sp])
+    fresh.step(5)
+    assert fresh.synchronize() == 0
+    assert fresh.diagnostics()["step"] == 5
+
+
+def test_energy_above_the_null_collision_bound_is_reported(env):
+    """Electrons far above E_cap make candidates whose collision rate exceeds
+    nu_max: the step flags PIC_EENERGYCAP and counts them (the null-collision
+    method of Sec. 2.2 needs nu <= nu_max)."""
+    pic, O = env
+    p = W.single_diode_small()
+    p.update(V=0.0, n_gas=1e24, E_cap_e_eV=1.0, gamma_emit=0.0, window_start=0)
+    n = 20000
+    rng = np.random.default_rng(18)
+    v = math.sqrt(2 * 50.0 * W.E_CHARGE / W.M_E)
+    z = ((0.2 + 0.6 * rng.random(n)) * p["L"]).astype(np.float32)
+    zero = np.zeros(n, np.float32)
+    d = pic.Diode(p)
+    d.inject(0, z, zero, zero, np.full(n, v, np.float32))
+    d.step(1)
+    assert d.synchronize() == pic.PIC_EENERGYCAP
+    dg = d.diagnostics(check=False)
+    assert dg["rc"] == pic.PIC_EENERGYCAP and dg["energy_cap_exceeded"] > 100
