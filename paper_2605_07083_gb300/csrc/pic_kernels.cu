@@ -1,17 +1,22 @@
 // pic_kernels.cu -- sm_103a kernels of one PIC-MCC time step
 // (arXiv 2605.07083, Sec. 2.1-2.2):
 //
-//   k_push  : gather E(z) from shared memory, leapfrog push (only v_z is
-//             accelerated, 1D-3V), absorbing electrodes, null-collision MCC
-//             candidates on a Philox counter stream, and the fixed-point
-//             charge deposit of the survivors into a per-block shared-memory
-//             histogram flushed with 64-bit integer atomics.  One streaming
-//             pass over z, v_z, id (128-bit vector loads/stores).
-//   k_post  : one block per diode: ordered absorbed-slot lists -> boundary
-//             tallies, deterministic hole-filling compaction, ionisation
-//             children (by parent id), thermionic emission, ion-loss
-//             replenishment, their deposit, and the FP64 Poisson/E solve.
-//   k_field : the Poisson/E solve alone (after a full deposit).
+//   k_push    : gather E(z) from shared memory, leapfrog push (only v_z is
+//               accelerated, 1D-3V), absorbing electrodes, the null-collision
+//               candidate test on a Philox2x32 counter stream, and the
+//               fixed-point charge deposit of the survivors into a per-block
+//               shared-memory histogram flushed with 64-bit integer atomics.
+//               One streaming pass over z, v_z, id, staged per warp by bulk
+//               copies into shared memory.
+//   k_mcc     : the collisions of the step's candidates.
+//   k_post    : three blocks per diode, one per species: ordered absorbed-slot
+//               lists -> boundary tallies, deterministic hole-filling
+//               compaction, then the species' appends (thermionic emission;
+//               ionisation children by parent id and ion-loss replenishment)
+//               and their deposit; the last of the three solves E in FP64.
+//   k_field   : the Poisson/E solve alone (after a full deposit).
+//   k_phi     : phi and E of the current state, on request.
+//   k_profile : per-species density samples of the late-time profiles.
 #include "pic_internal.cuh"
 
 namespace pic {
