@@ -38,7 +38,9 @@ enum {
     PIC_EINVAL = -1,      /* bad argument or configuration */
     PIC_ENOMEM = -2,      /* device allocation failed */
     PIC_ECUDA = -3,       /* a CUDA runtime call failed */
-    PIC_ECAPACITY = -4,   /* a species outgrew its capacity; extra particles dropped */
+    PIC_ECAPACITY = -4,   /* a species outgrew its capacity (extra particles dropped), or a
+                             diode used up its 2^32 particle ids (ids key the random
+                             streams, so they are not reused) */
     PIC_ETIMEOUT = -5,    /* a bounded device wait gave up */
     PIC_EENERGYCAP = -6   /* a collision candidate exceeded the null-collision bound */
 };

@@ -1120,6 +1120,11 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post(DevState st) {
   if (tid == 0) {
     const int Pt = ic.replenish ? sD[2] : 0;
     dyn->next_id = id_repl + 2u * (uint32_t)Pt;
+    // ids key the random streams: a diode that has handed out all 2^32 of
+    // them would reuse one, so that is reported as running out of capacity
+    if ((unsigned long long)base_id + 2ull * (unsigned)E + (unsigned)Nemit + 2ull * (unsigned)Pt >
+        0xFFFFFFFFull)
+      atomicOr(&dyn->err, ERR_CAPACITY);
     if (step >= ic.window_start) {
       dyn->win_steps += 1;
       for (int k = 0; k < 3; ++k)

@@ -113,3 +113,27 @@ def test_load_rejects_other_runs_and_damaged_buffers(pic):
     d.load(blob)                        # the intact buffer still loads
     assert d.diagnostics()["step"] == 7
     assert d.diagnostics()["n_live"] == b.diagnostics()["n_live"]
+
+
+def test_running_out_of_particle_ids_is_reported(pic):
+    """A diode whose id counter is about to pass 2^32 reports PIC_ECAPACITY
+    instead of reusing ids (they key the random streams).  The counter is set
+    by editing a checkpoint: 56-byte header, the configs, capacities and live
+    counts (4 bytes per segment each), then the per-diode records, whose
+    next-id field follows the 8-byte step."""
+    import struct
+    p = W.single_diode_small(seed=6)          # ~19 electrons emitted per step
+    d = pic.Diode(p)
+    d.step(2)
+    blob = bytearray(d.save())
+    cfg_bytes = pic.load().pic_sizeof(0)
+    at = 56 + cfg_bytes + 2 * 3 * 4 + 8
+    # nothing has left the gap yet: every id handed out is a live particle
+    assert struct.unpack_from("<I", blob, at)[0] == sum(d.diagnostics()["n_live"])
+    struct.pack_into("<I", blob, at, 0xFFFFFFFF - 30)
+    c = pic.Diode(p)
+    c.load(bytes(blob))
+    c.step(1)
+    assert c.synchronize() == 0                # 30 ids left, ~19 used
+    c.step(3)
+    assert c.synchronize() == pic.PIC_ECAPACITY
