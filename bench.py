@@ -245,6 +245,8 @@ def run_ours(args, rank, world):
     achieved = ALG_BYTES_PER_PARTICLE * n_per_launch / (push_ms * 1e-3) / 1e9
     cpu = cpu_baseline(p, state) if not args.no_cpu else None
     batched = run_batched() if not args.no_batched else None
+    if batched is not None and not args.no_cpu:
+        batched["cpu_baseline"] = cpu_baseline_batched()
     small = run_small() if not args.no_batched else None
     launches = 3 * args.steps
     out = {
@@ -277,20 +279,60 @@ def run_ours(args, rank, world):
     return out
 
 
+def batched_instance(p, i, seed=1000, steps=100):
+    """Diode i of the sweep preloaded with its target in-flight emitted
+    population (uniform positions, T_w velocities); sets its capacities."""
+    n = int(p["target_in_flight"])
+    rng = np.random.default_rng(seed + 7919 * (i + 1))
+    em = W.emitted_fill(rng, n, p["L"], p["T_wall_K"])
+    em = (W.clamp_inside(em[0], p["L"]),) + tuple(em[1:])
+    x = p["gamma_emit"] * p["dt"] / p["weight"]
+    p["capacity"] = (int(n + 1.3 * x * (3 * steps + 400)) + 4096, 65536, 65536)
+    return em
+
+
 def batched_workload(n_instances=64, seed=1000, steps=100):
-    """The uneven 64-diode sweep, each diode preloaded with its target
-    in-flight emitted population (uniform positions, T_w velocities)."""
+    """The uneven 64-diode sweep, each diode preloaded (batched_instance)."""
     ps = W.batched_sweep(n_instances=n_instances, seed=seed, n_steps=steps)
-    states = []
-    for i, p in enumerate(ps):
-        n = int(p["target_in_flight"])
-        rng = np.random.default_rng(seed + 7919 * (i + 1))
-        em = W.emitted_fill(rng, n, p["L"], p["T_wall_K"])
-        em = (W.clamp_inside(em[0], p["L"]),) + tuple(em[1:])
-        x = p["gamma_emit"] * p["dt"] / p["weight"]
-        p["capacity"] = (int(n + 1.3 * x * (3 * steps + 400)) + 4096, 65536, 65536)
-        states.append(em)
+    states = [batched_instance(p, i, seed, steps) for i, p in enumerate(ps)]
     return ps, states
+
+
+def _oracle_instance(args):
+    """One sweep diode on the oracle (a worker process): (particle-steps, s)."""
+    i, n_steps = args
+    from oracle import oracle as O
+    p = W.batched_sweep(n_instances=64, seed=1000, n_steps=100)[i]
+    em = batched_instance(p, i)
+    o = O.Oracle(p)
+    o.inject(0, *em)
+    ps = 0
+    t0 = time.perf_counter()
+    for _ in range(n_steps):
+        n = o.count(0) + o.count(1) + o.count(2)
+        o.step(1)
+        ps += n
+    el = time.perf_counter() - t0
+    o.close()
+    return ps, el
+
+
+def cpu_baseline_batched(n_steps=16):
+    """The 64 sweep diodes as independent oracle processes over all host
+    cores (a bounded number of steps each, from the same preload)."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(min(cores, 64)) as pool:
+        res = pool.map(_oracle_instance, [(i, n_steps) for i in range(64)], chunksize=1)
+    wall = time.perf_counter() - t0
+    ps = sum(r[0] for r in res)
+    busy = sum(r[1] for r in res)
+    return {"value": ps / busy * min(cores, 64), "unit": "particle-steps/s", "cores": min(cores, 64),
+            "kind": "oracle",
+            "sample": "64 sweep diodes, %d steps each from the preload, one process per core; "
+                      "value = particle-steps / summed step time x cores (%.1f s wall incl. "
+                      "start-up)" % (n_steps, wall)}
 
 
 def run_batched(steps=100, warmup=20):
