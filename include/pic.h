@@ -205,7 +205,9 @@ int pic_get_state(pic_handle* h, int instance, int species, float* z, float* vx,
 int pic_get_rho_fixed(pic_handle* h, int instance, int64_t* out, int64_t n_nodes);
 
 /* phi (V, FP64) and E (V/m, the FP32 copy the push gathers) on the nodes
- * for the current state; either pointer may be NULL.  Synchronises. */
+ * for the current state; either pointer may be NULL.  A time step solves E
+ * only; this call solves phi (and E, identically) from the current charge on
+ * the handle's stream.  Synchronises. */
 int pic_get_field(pic_handle* h, int instance, double* phi, float* E, int64_t n_nodes);
 
 /* ---- late-time profiles and the virtual-cathode estimate (Sec. 3) -----
