@@ -110,7 +110,9 @@ typedef struct pic_allocator {
 /* Launch shape and scheduling knobs (pic_tune).  Zero keeps the current value. */
 typedef struct pic_tuning {
     uint32_t size;            /* sizeof(pic_tuning) */
-    int32_t push_threads;     /* threads per block of the particle kernels (64..256, multiple of 32) */
+    int32_t push_threads;     /* threads per block of the particle kernels (64..384, multiple of
+                                 32; default: the size that keeps closest to 24 resident warps
+                                 per SM for the handle's cell count, 256 when that ties) */
     int32_t push_blocks_per_sm;  /* cap on resident blocks per SM (default: occupancy limit) */
     int32_t sort_period;      /* counting sort by cell every this many steps; < 0 disables */
     int32_t graph_steps;      /* steps captured per CUDA graph; < 0 disables graphs */

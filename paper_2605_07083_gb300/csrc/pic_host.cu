@@ -64,6 +64,7 @@ struct pic_handle {
   int sm_count = 0;
   int push_threads = 256, blocks_per_sm = 0, G = 0;   // 0 blocks/SM: occupancy limit
   int sort_period = 0, graph_steps = 50;
+  bool threads_set = false;     // push_threads chosen by the caller (pic_tune)
   DevState st{};
   std::vector<Alloc> allocs;
   bool dirty = true;
@@ -266,12 +267,35 @@ cudaError_t raise_smem_limits(int device) {
   return e;
 }
 
+size_t push_smem_bytes(const pic_handle* h, int threads) {
+  return (((size_t)h->max_nodes * 20 + 8 + (size_t)(h->n_seg + 1) * 8 + 127) & ~(size_t)127) +
+         (size_t)(threads / 32) * 2 * (kStageBytes + 8);
+}
+
+// Default threads per push block: the push is issue-bound, and on this part
+// about 24 resident warps per SM hide its latencies best (more contend for
+// issue slots, fewer leave dependency waits exposed).  The shared-memory
+// footprint grows with the cell count, so pick the block size that gets
+// closest to 24 warps from below, preferring 256 threads on ties.
+int default_push_threads(const pic_handle* h) {
+  int best = 256, best_w = -1;
+  for (int t : {256, 128, 160, 192, 224, 288, 320, 352, 384}) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push, t, push_smem_bytes(h, t)) !=
+        cudaSuccess)
+      continue;
+    const int w = std::min(occ * t / 32, 24);
+    if (w > best_w) { best = t; best_w = w; }
+  }
+  return best;
+}
+
 int set_launch_shape(pic_handle* h) {
-  h->push_smem = (((size_t)h->max_nodes * 20 + 8 + (size_t)(h->n_seg + 1) * 8 + 127) & ~(size_t)127) +
-                 (size_t)(h->push_threads / 32) * 2 * (kStageBytes + 8);
-  h->field_smem = (size_t)h->max_nodes * 8;
   cudaError_t e = raise_smem_limits(h->device);
   if (e != cudaSuccess) return cuda_fail(h, e);
+  if (!h->threads_set) h->push_threads = default_push_threads(h);
+  h->push_smem = push_smem_bytes(h, h->push_threads);
+  h->field_smem = (size_t)h->max_nodes * 8;
   int occ = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push, h->push_threads, h->push_smem);
   if (e != cudaSuccess) return cuda_fail(h, e);
@@ -1133,8 +1157,9 @@ int pic_load(pic_handle* h, const void* host_buf, size_t bytes) {
 int pic_tune(pic_handle* h, const pic_tuning* t) {
   if (!h || !t || t->size != sizeof(pic_tuning)) return PIC_EINVAL;
   if (t->push_threads != 0) {
-    if (t->push_threads < 64 || t->push_threads > 256 || t->push_threads % 32) return PIC_EINVAL;
+    if (t->push_threads < 64 || t->push_threads > 384 || t->push_threads % 32) return PIC_EINVAL;
     h->push_threads = t->push_threads;
+    h->threads_set = true;
   }
   if (t->push_blocks_per_sm != 0) {
     if (t->push_blocks_per_sm < 1 || t->push_blocks_per_sm > 32) return PIC_EINVAL;

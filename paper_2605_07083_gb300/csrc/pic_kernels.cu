@@ -616,7 +616,7 @@ __device__ __forceinline__ void push_body(const DevState& st) {
   }
 }
 
-__global__ void __launch_bounds__(256, 3) k_push(DevState st) { push_body<false>(st); }
+__global__ void __launch_bounds__(384, 2) k_push(DevState st) { push_body<false>(st); }
 __global__ void k_deposit(DevState st) { push_body<true>(st); }
 
 // ------------------------------------------------------------------ field solve
