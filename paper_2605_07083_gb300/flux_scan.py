@@ -29,6 +29,23 @@ _DIAG_KEYS = ("gamma_emit", "gamma_emit_realized", "gamma_ref", "gamma_net", "ga
               "q_anode_total_2", "window_time", "window_steps", "energy_cap_exceeded")
 
 
+def stationarity(blocks) -> dict:
+    """Reading of Sec. 3's "late-time window" check: split the window's block
+    means (equal-length blocks of steps) into halves and call the window
+    stationary when the two half means differ by no more than twice the
+    standard error of their difference, sqrt(s1^2/n1 + s2^2/n2) from the
+    block scatter.  Needs at least two blocks per half."""
+    b = np.asarray([x for x in blocks if np.isfinite(x)], np.float64)
+    if b.size < 4:
+        return {"blocks": b.size, "stationary": None}
+    h = b.size // 2
+    a, c = b[:h], b[b.size - h:]
+    se = math.sqrt(a.var(ddof=1) / a.size + c.var(ddof=1) / c.size)
+    diff = float(c.mean() - a.mean())
+    return {"blocks": int(b.size), "first_half": float(a.mean()), "second_half": float(c.mean()),
+            "difference": diff, "two_sigma": 2.0 * se, "stationary": bool(abs(diff) <= 2.0 * se)}
+
+
 def run(fluxes=W.TABLE2_FLUXES, ppc=1000, n_steps=4_500_000, window_start=None,
         profile_period=1000, chunk=50_000, max_seconds=None, seed=3, log=sys.stderr,
         profile_points=512, table3=False) -> dict:
@@ -52,11 +69,21 @@ def run(fluxes=W.TABLE2_FLUXES, ppc=1000, n_steps=4_500_000, window_start=None,
     pushed0 = sum(d.diagnostics(i)["particles_pushed"] for i in range(len(ps)))
     ev0.record(d.stream)
     done, complete = 0, True
+    # block means of the backflow ratio inside the window, one per chunk
+    prev = [None] * len(ps)
+    blocks = [[] for _ in ps]
     while done < n_steps:
         n = min(chunk, n_steps - done)
         d.step(n)
         d.synchronize()
         done += n
+        for i, p in enumerate(ps):
+            dg = d.diagnostics(i, check=False)
+            cur = (dg["window_steps"], int(dg["count"][0][0]))
+            if prev[i] is not None and cur[0] - prev[i][0] == n:
+                dt = n * p["dt"]
+                blocks[i].append((cur[1] - prev[i][1]) * p["weight"] / dt / p["gamma_emit"])
+            prev[i] = cur
         el = time.time() - t0
         live = [sum(d.diagnostics(i)["n_live"]) for i in range(len(ps))]
         print("step %d/%d  %.0f s  live %.3g" % (done, n_steps, el, float(sum(live))), file=log,
@@ -75,6 +102,8 @@ def run(fluxes=W.TABLE2_FLUXES, ppc=1000, n_steps=4_500_000, window_start=None,
                "label": p.get("label", ""), "ppc": p["ppc"], "n_live": dg["n_live"],
                "rc": dg["rc"], "collisions": dg["collisions"].tolist()}
         row.update({k: dg[k] for k in _DIAG_KEYS})
+        row["backflow_blocks"] = blocks[i]
+        row["stationarity"] = stationarity(blocks[i])
         prof = d.profiles(i)
         if prof["samples"] > 0:
             vc = d.virtual_cathode(i, near_fraction=0.05)
@@ -120,10 +149,12 @@ def main(argv=None):
             f.write(txt)
     print(json.dumps({k: v for k, v in res.items() if k != "rows"}))
     for r in res["rows"]:
-        print("%-12s %6.2f  backflow %.4f  net %.4f  anode %.4f  q_cool1 %.2f  phi_eff %s" % (
-            r["label"], r["gamma_emit_1e19"], r["backflow_ratio"], r["net_efficiency"],
-            r["collection_efficiency"], r["q_cooling_1"],
-            "%.4f" % r["virtual_cathode"]["phi_vc_eff"] if "virtual_cathode" in r else "-"))
+        print("%-12s %6.2f  backflow %.4f  net %.4f  anode %.4f  q_cool1 %.2f  phi_eff %s  "
+              "stationary %s" % (
+                  r["label"], r["gamma_emit_1e19"], r["backflow_ratio"], r["net_efficiency"],
+                  r["collection_efficiency"], r["q_cooling_1"],
+                  "%.4f" % r["virtual_cathode"]["phi_vc_eff"] if "virtual_cathode" in r else "-",
+                  r["stationarity"]["stationary"]))
 
 
 if __name__ == "__main__":

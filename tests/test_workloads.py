@@ -49,3 +49,18 @@ def test_initial_plasma_is_uniform_and_maxwellian():
         s = math.sqrt(W.E_CHARGE * T / m)
         for v in (vx, vy, vz):
             assert abs(v.std() / s - 1) < 0.02 and abs(v.mean()) < 0.02 * s
+
+
+def test_window_stationarity_check():
+    """Block means that scatter around one value are stationary; a drift of
+    many standard errors between the halves is not; too few blocks give no
+    verdict."""
+    from paper_2605_07083_gb300.flux_scan import stationarity
+    rng = np.random.default_rng(5)
+    flat = 0.47 + 0.005 * rng.standard_normal(12)
+    assert stationarity(flat)["stationary"] is True
+    drift = 0.40 + 0.01 * np.arange(12) + 0.002 * rng.standard_normal(12)
+    r = stationarity(drift)
+    assert r["stationary"] is False and r["difference"] > r["two_sigma"]
+    assert stationarity([0.5, 0.5, 0.5])["stationary"] is None
+    assert stationarity([0.4, float("nan"), 0.41, 0.4, 0.42])["blocks"] == 4
