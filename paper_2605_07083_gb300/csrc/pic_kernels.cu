@@ -178,7 +178,8 @@ __device__ __forceinline__ void deposit_warp(const Hist& h, const float (&z)[4],
 // Returns the new v_z; writes v_x, v_y in place.  Rare path: kept out of line.
 __device__ __forceinline__ float collide(const InstConst* __restrict__ icg, InstDyn* dyn,
                                       Event* evb, float* vxp, float* vyp, int sp, uint32_t pid,
-                                      uint32_t stepw, long long step, float z, float vz) {
+                                      uint32_t stepw, long long step, float z, float vz,
+                                      int& code_out) {
   const InstConst& ic = *icg;
   const uint32_t k0 = ic.key0[sp], k1 = ic.key1;
   const uint4 A = philox10(make_uint4(pid, stepw, 0u, TAG_MCC), k0, k1);
@@ -268,10 +269,7 @@ __device__ __forceinline__ float collide(const InstConst* __restrict__ icg, Inst
       nvz = fm * vz + fM * vnz + fM * gm * dz;
     }
   }
-  if (in_win) {
-    atomicAdd(&dyn->cand[sp], 1ull);
-    atomicAdd(&dyn->coll[code], 1ull);
-  }
+  code_out = code;
   if (code != 0) {
     *vxp = nvx;
     *vyp = nvy;
@@ -288,10 +286,24 @@ __global__ void __launch_bounds__(kMccThreads) k_mcc(DevState st) {
     const long long slot = st.seg_off[g] + (long long)(e & 0xffffffffu);
     const int inst = g / 3, sp = g - 3 * inst;
     const long long step = st.dyn[inst].step;
+    int code;
     const float vz = collide(st.ic + inst, st.dyn + inst, st.ev_buf + (long long)inst * kEvCap,
                              st.vx + slot, st.vy + slot, sp, st.id[slot], (uint32_t)step, step,
-                             st.z[slot], st.vz[slot]);
+                             st.z[slot], st.vz[slot], code);
     st.vz[slot] = vz;
+    if (step >= st.ic[inst].window_start) {
+      // window tallies of candidates and outcomes: lanes with the same
+      // (segment, outcome) add once -- one 64-bit atomic per candidate on a
+      // handful of per-diode counters would serialise when candidates are
+      // many (about 1 % of the particles per step at 40 V)
+      const unsigned mask = __activemask();
+      const unsigned peers = __match_any_sync(mask, ((unsigned)g << 3) | (unsigned)code);
+      if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) {
+        const unsigned long long c = (unsigned long long)__popc(peers);
+        atomicAdd(&st.dyn[inst].cand[sp], c);
+        atomicAdd(&st.dyn[inst].coll[code], c);
+      }
+    }
   }
 }
 

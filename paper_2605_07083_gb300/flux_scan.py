@@ -48,7 +48,7 @@ def stationarity(blocks) -> dict:
 
 def run(fluxes=W.TABLE2_FLUXES, ppc=1000, n_steps=4_500_000, window_start=None,
         profile_period=1000, chunk=50_000, max_seconds=None, seed=3, log=sys.stderr,
-        profile_points=512, table3=False) -> dict:
+        profile_points=512, table3=False, kernel_times=0) -> dict:
     """Run the scan (or, with table3, the Table 3 sensitivity cases) as one
     batched job; stop early (and say so) if max_seconds would be passed."""
     import torch
@@ -113,6 +113,20 @@ def run(fluxes=W.TABLE2_FLUXES, ppc=1000, n_steps=4_500_000, window_start=None,
                                   "phi_V": prof["phi"][::stride].tolist()}
             row["profile_samples"] = prof["samples"]
         rows.append(row)
+    kt = None
+    if kernel_times > 0:
+        # after the rows: per-kernel device time (one launch at a time) and the
+        # CUDA-graph step, on the final state
+        prof = d.profile(kernel_times)
+        n = max(prof["steps"], 1)
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(d.stream)
+        d.step(1000)
+        g1.record(d.stream)
+        g1.synchronize()
+        kt = {"steps": n, "push_us": 1e3 * prof["ms_push"] / n, "mcc_us": 1e3 * prof["ms_mcc"] / n,
+              "post_us": 1e3 * prof["ms_post"] / n, "graph_step_us": g0.elapsed_time(g1),
+              "live": int(sum(sum(d.diagnostics(i, check=False)["n_live"]) for i in range(len(ps))))}
     d.close()
     return {"config": {"fluxes_1e19": list(fluxes), "ppc": ppc, "n_steps": n_steps,
                        "steps_done": done, "complete": complete,
@@ -120,6 +134,7 @@ def run(fluxes=W.TABLE2_FLUXES, ppc=1000, n_steps=4_500_000, window_start=None,
                        "dt_s": ps[0]["dt"], "weight_m2": ps[0]["weight"], "L_m": ps[0]["L"],
                        "Nz": ps[0]["Nz"], "V": ps[0]["V"], "E_cap_eV": ps[0]["E_cap_e_eV"]},
             "rows": rows,
+            "kernel_times": kt,
             "gpu_ms": ms, "particle_steps": int(pushed),
             "particle_steps_per_s": pushed / (ms * 1e-3) if ms > 0 else math.nan,
             "wall_s": time.time() - t0}
@@ -137,12 +152,14 @@ def main(argv=None):
                     help="comma-separated fluxes in 1e19 m^-2 s^-1 (default: Table 2)")
     ap.add_argument("--table3", action="store_true",
                     help="run the Table 3 sensitivity cases instead of the flux scan")
+    ap.add_argument("--kernel-times", type=int, default=0,
+                    help="after the run, time this many steps kernel by kernel and 1000 as graphs")
     ap.add_argument("--out", type=str, default=None)
     a = ap.parse_args(argv)
     fl = tuple(float(x) for x in a.fluxes.split(",")) if a.fluxes else W.TABLE2_FLUXES
     res = run(fl, ppc=a.ppc, n_steps=a.steps, window_start=a.window_start,
               profile_period=a.profile_period, chunk=a.chunk, max_seconds=a.max_seconds,
-              table3=a.table3)
+              table3=a.table3, kernel_times=a.kernel_times)
     txt = json.dumps(res)
     if a.out:
         with open(a.out, "w") as f:
