@@ -115,7 +115,12 @@ typedef struct pic_tuning {
                                  per SM for the handle's cell count, 256 when that ties) */
     int32_t push_blocks_per_sm;  /* cap on resident blocks per SM (default: occupancy limit) */
     int32_t sort_period;      /* counting sort by cell every this many steps; < 0 disables */
-    int32_t graph_steps;      /* steps captured per CUDA graph; < 0 disables graphs */
+    int32_t graph_steps;      /* longest step loop captured as one CUDA graph (default 64);
+                                 every power of two below it is captured too, so pic_step(n)
+                                 runs any n as graphs.  With a periodic sort only the
+                                 full-length graph exists and runs on sort-aligned steps.
+                                 All of them are built by the first pic_step after a change
+                                 of launch shape.  < 0 disables graphs */
     int32_t wait_polls;       /* polls of a bulk-copy wait in the push kernel before it gives
                                  up with PIC_ETIMEOUT (default 2^20, each suspending the warp
                                  up to ~1 us): n > 0 sets n; -1 gives up without polling, a
@@ -314,9 +319,10 @@ const char* pic_last_error(const pic_handle* h);
  * z..id: n input particles (device); z_out..id_out: n outputs (device), not
  * aliasing the inputs.  Output = input stably sorted by the fixed-point cell
  * rule with Nz = n_cells, L = gap_m (the same order as pic_sort).  Enqueued
- * on cuda_stream.  Limits: n_cells * ceil(n / 8192) <= 2^20 (for example
- * 4.19M particles over 2048 cells) and 1 <= n_cells <= 4096; beyond them it
- * returns PIC_ECAPACITY without launching anything.  The first call on each
+ * on cuda_stream.  Limits: n <= 2^31 - 1 (positions are 32-bit), n_cells *
+ * ceil(n / 8192) <= 2^20 (for example 4.19M particles over 2048 cells) and
+ * 1 <= n_cells <= 4096; beyond them it returns PIC_ECAPACITY (PIC_EINVAL for
+ * a bad n_cells) without launching anything.  The first call on each
  * device sets up that device (it looks up the scratch's device address and
  * raises a kernel attribute) and should come before any stream capture.
  * Every call shares the one scratch array and overwrites all of it that it

@@ -63,7 +63,7 @@ struct pic_handle {
   int total_nodes = 0, max_nodes = 0;
   int sm_count = 0;
   int push_threads = 256, blocks_per_sm = 0, G = 0;   // 0 blocks/SM: occupancy limit
-  int sort_period = 0, graph_steps = 50;
+  int sort_period = 0, graph_steps = 64;
   bool threads_set = false;     // push_threads chosen by the caller (pic_tune)
   DevState st{};
   std::vector<Alloc> allocs;
@@ -71,8 +71,9 @@ struct pic_handle {
   int sticky = PIC_OK;
   int64_t host_step = 0;        // mirror of the device step counter
   int64_t last_sort_step = 0;
-  cudaGraphExec_t graph = nullptr;
-  int graph_len = 0;
+  // captured step loops, longest first: graph_steps steps, then every power
+  // of two below it, so that any step count runs as graphs
+  std::vector<std::pair<int, cudaGraphExec_t>> graphs;
   size_t push_smem = 0, post_smem = 0, field_smem = 0;
   size_t dcount_ints = 0;
   int bstart_len = 0;
@@ -232,9 +233,8 @@ int check_flags(pic_handle* h) {
 }
 
 void drop_graph(pic_handle* h) {
-  if (h->graph) cudaGraphExecDestroy(h->graph);
-  h->graph = nullptr;
-  h->graph_len = 0;
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
+  h->graphs.clear();
 }
 
 // dynamic shared memory a kernel may request: the opt-in maximum less its
@@ -406,8 +406,8 @@ cudaError_t launch_step(pic_handle* h) {
   return cudaGetLastError();
 }
 
-int build_graph(pic_handle* h, int len) {
-  drop_graph(h);
+int build_graph(pic_handle* h, int len, cudaGraphExec_t* out) {
+  *out = nullptr;
   cudaGraph_t g = nullptr;
   const int64_t saved = h->host_step;
   cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
@@ -421,13 +421,37 @@ int build_graph(pic_handle* h, int len) {
   }
   e = cudaStreamEndCapture(h->stream, &g);
   if (e != cudaSuccess) return cuda_fail_at(h, e, "cudaStreamEndCapture");
-  e = cudaGraphInstantiate(&h->graph, g, 0);
+  e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
-    h->graph = nullptr;
+    *out = nullptr;
     return cuda_fail_at(h, e, "cudaGraphInstantiate");
   }
-  h->graph_len = len;
+  return PIC_OK;
+}
+
+// All step graphs of the handle at once (the first pic_step after a change
+// of launch shape pays for them): graph_steps steps, and 2^k steps for every
+// 2^k < graph_steps.  With a periodic sort only the full-length graph is
+// built; it is launched on sort-aligned steps only.
+int build_graphs(pic_handle* h) {
+  drop_graph(h);
+  std::vector<int> lens{h->graph_steps};
+  if (h->sort_period <= 0) {
+    int p2 = 1;
+    while (p2 * 2 < h->graph_steps) p2 *= 2;
+    for (; p2 >= 1; p2 /= 2)
+      if (p2 < h->graph_steps) lens.push_back(p2);
+  }
+  for (int len : lens) {
+    cudaGraphExec_t g = nullptr;
+    int rc = build_graph(h, len, &g);
+    if (rc != PIC_OK) {
+      drop_graph(h);
+      return rc;
+    }
+    h->graphs.push_back({len, g});
+  }
   return PIC_OK;
 }
 
@@ -722,20 +746,24 @@ int pic_step(pic_handle* h, int64_t n_steps) {
   if (rc != PIC_OK) return rc;
   int64_t left = n_steps;
   const int len = h->graph_steps;
-  // a captured graph bakes in where the periodic sort falls: use it only on
-  // sort-aligned starts with a sort-aligned length
+  // a captured graph bakes in where the periodic sort falls: with a sort,
+  // only sort-aligned starts with a sort-aligned length run as a graph
   const bool aligned = h->sort_period <= 0 ||
                        (len % h->sort_period == 0 && h->host_step % h->sort_period == 0);
-  if (len > 0 && aligned) {
-    while (left >= len) {
-      if (!h->graph || h->graph_len != len) {
-        rc = build_graph(h, len);
-        if (rc != PIC_OK) return rc;
+  if (len > 0 && aligned && (h->sort_period <= 0 || left >= len)) {
+    if (h->graphs.empty() || h->graphs[0].first != len) {
+      rc = build_graphs(h);
+      if (rc != PIC_OK) return rc;
+    }
+    // longest first: n steps run as floor(n / graph_steps) full graphs and
+    // the binary digits of the rest
+    for (const auto& g : h->graphs) {
+      while (left >= g.first) {
+        cudaError_t e = cudaGraphLaunch(g.second, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e);
+        h->host_step += g.first;
+        left -= g.first;
       }
-      cudaError_t e = cudaGraphLaunch(h->graph, h->stream);
-      if (e != cudaSuccess) return cuda_fail(h, e);
-      h->host_step += len;
-      left -= len;
     }
   }
   for (; left > 0; --left) {

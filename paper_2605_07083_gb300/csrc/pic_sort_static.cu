@@ -7,6 +7,7 @@
 // scratch taken from g_static_hist instead of a handle.
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <mutex>
 
 #include "../../include/pic.h"
@@ -156,6 +157,8 @@ extern "C" int pic_sort_by_cell_static(const float* z, const float* vx, const fl
   if (n == 0) return PIC_OK;
   if (!z || !vx || !vy || !vz || !id || !z_out || !vx_out || !vy_out || !vz_out || !id_out)
     return PIC_EINVAL;
+  // histogram entries and output positions are 32-bit
+  if (n > (int64_t)INT32_MAX) return PIC_ECAPACITY;
   const long long nch = (n + kChunk - 1) / kChunk;
   if ((long long)n_cells * nch > kStaticHistInts) return PIC_ECAPACITY;
   int dev = 0;

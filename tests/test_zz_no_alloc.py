@@ -64,5 +64,10 @@ def test_static_sort_rejects_sizes_beyond_its_scratch():
     rc = lib.pic_sort_by_cell_static(ptr, ptr, ptr, ptr, ptr, 3_000_000, 4096, 1e-3,
                                      ptr, ptr, ptr, ptr, ptr, None)
     assert rc == pic.PIC_ECAPACITY
+    # one cell keeps the histogram small, but 2^31 particles would overflow
+    # the 32-bit output positions: refused before any launch
+    rc = lib.pic_sort_by_cell_static(ptr, ptr, ptr, ptr, ptr, 1 << 31, 1, 1e-3,
+                                     ptr, ptr, ptr, ptr, ptr, None)
+    assert rc == pic.PIC_ECAPACITY
     assert lib.pic_sort_by_cell_static(ptr, ptr, ptr, ptr, ptr, 10, 0, 1e-3,
                                        ptr, ptr, ptr, ptr, ptr, None) == pic.PIC_EINVAL
