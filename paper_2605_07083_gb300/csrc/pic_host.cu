@@ -77,6 +77,7 @@ struct pic_handle {
   size_t push_smem = 0, post_smem = 0, field_smem = 0;
   size_t dcount_ints = 0;
   int bstart_len = 0;
+  int bw_len = 0;
   int mcc_blocks = 0;
   bool sort_ready = false;
   int sort_chunks = 1;
@@ -276,10 +277,11 @@ size_t push_smem_bytes(const pic_handle* h, int threads) {
 // about 24 resident warps per SM hide its latencies best (more contend for
 // issue slots, fewer leave dependency waits exposed).  The shared-memory
 // footprint grows with the cell count, so pick the block size that gets
-// closest to 24 warps from below, preferring 256 threads on ties.
+// closest to 24 warps from below, preferring 384 threads (two blocks per
+// SM) on ties.
 int default_push_threads(const pic_handle* h) {
-  int best = 256, best_w = -1;
-  for (int t : {256, 128, 160, 192, 224, 288, 320, 352, 384}) {
+  int best = 384, best_w = -1;
+  for (int t : {384, 256, 128, 160, 192, 224, 288, 320, 352}) {
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push, t, push_smem_bytes(h, t)) !=
         cudaSuccess)
@@ -301,9 +303,9 @@ int set_launch_shape(pic_handle* h) {
   if (e != cudaSuccess) return cuda_fail(h, e);
   if (occ < 1) occ = 1;
   const int per_sm = h->blocks_per_sm > 0 ? std::min(h->blocks_per_sm, occ) : occ;
-  // enough blocks that none holds more than kPushMaxParticlesPerBlock slots
-  const int64_t min_blocks = (h->total_cap + kPushMaxParticlesPerBlock - 1) / kPushMaxParticlesPerBlock;
-  h->G = (int)std::max<int64_t>((int64_t)h->sm_count * per_sm, min_blocks);
+  // one wave: every block resident at once (a block flushes its histogram
+  // after every kSubQuads quads, so its share has no upper bound)
+  h->G = h->sm_count * per_sm;
   h->st.G = h->G;
   h->st.W = h->push_threads / 32;
   h->mcc_blocks = h->sm_count;
@@ -313,6 +315,25 @@ int set_launch_shape(pic_handle* h) {
     if (!p) return PIC_ENOMEM;
     h->st.dcount = (int32_t*)p;
     h->dcount_ints = need;
+  }
+  // push-block weights back to equal shares; their times unknown
+  if (h->G > h->bw_len) {
+    void* p = dev_alloc(h, sizeof(long long) * (size_t)(h->G + 1) + sizeof(int) * 2 * (size_t)h->G);
+    if (!p) return PIC_ENOMEM;
+    h->st.bwp = (long long*)p;
+    h->bw_len = h->G;
+  }
+  h->st.bw = (int*)(h->st.bwp + h->G + 1);
+  h->st.bt = h->st.bw + h->G;
+  {
+    std::vector<long long> w((size_t)h->G + 1 + h->G, 0);
+    for (int b = 0; b <= h->G; ++b) w[b] = (long long)b * kNominalWeight;
+    int* wi = reinterpret_cast<int*>(w.data() + h->G + 1);
+    for (int b = 0; b < h->G; ++b) wi[b] = kNominalWeight;
+    const size_t bytes = sizeof(long long) * (size_t)(h->G + 1) + sizeof(int) * 2 * (size_t)h->G;
+    cudaError_t e2 = cudaMemcpyAsync(h->st.bwp, w.data(), bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(h->stream);
+    if (e2 != cudaSuccess) return cuda_fail(h, e2);
   }
   if (h->G + 1 > h->bstart_len) {
     void* p = dev_alloc(h, sizeof(int64_t) * (size_t)(h->G + 1));
@@ -325,11 +346,12 @@ int set_launch_shape(pic_handle* h) {
   const size_t species = (size_t)kDeadSmem * 4 + (size_t)(h->G + 1) * 12 + 16;
   const size_t tail = std::max((size_t)kEvCap * 8, (size_t)h->max_nodes * 8 + 16);
   h->post_smem = std::max(species, tail);
-  // profile sampler: blocks per segment so that none bins more than 2^20
-  // particles (its 32-bit counters), else about two blocks per SM in total
+  // profile sampler: blocks per segment so that none bins more than
+  // kHistMaxParticles particles (its 32-bit counters), else about two blocks
+  // per SM in total
   int64_t max_cap = 1;
   for (int32_t c : h->seg_cap) max_cap = std::max<int64_t>(max_cap, c);
-  const int64_t gmin = (max_cap + (1 << 20) - 1) >> 20;
+  const int64_t gmin = (max_cap + kHistMaxParticles - 1) / kHistMaxParticles;
   const int64_t gfill = std::min<int64_t>((max_cap + 8191) / 8192,
                                           std::max<int64_t>(1, 2 * h->sm_count / h->n_seg));
   h->prof_gx = (int)std::max<int64_t>(1, std::max(gmin, gfill));
@@ -1194,6 +1216,7 @@ int pic_tune(pic_handle* h, const pic_tuning* t) {
     h->blocks_per_sm = t->push_blocks_per_sm;
   }
   if (t->sort_period != 0) h->sort_period = t->sort_period < 0 ? 0 : t->sort_period;
+  h->st.agg = h->sort_period > 0 ? 1 : 0;
   if (t->graph_steps != 0) h->graph_steps = t->graph_steps < 0 ? 0 : t->graph_steps;
   if (t->wait_polls != 0) {
     if (t->wait_polls < -2) return PIC_EINVAL;

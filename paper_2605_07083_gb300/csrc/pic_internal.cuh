@@ -11,7 +11,11 @@ constexpr int kMaxNz = 4096;          // shared-memory grid limit (nodes = Nz + 
 constexpr int kMaxInstances = 1024;
 constexpr int kEvCap = 2048;          // ionisation events per instance per step
 constexpr int kPostThreads = 512;
-constexpr int kPushMaxParticlesPerBlock = 1 << 20;   // cell-counter lifetime
+constexpr int kHistMaxParticles = (1 << 20) - 256;
+// push-block weights (shares of the particle range): nominal, bounds
+constexpr int kNominalWeight = 1024, kMinWeight = 256, kMaxWeight = 4096;
+// quads a push block bins before it flushes its histogram
+constexpr int kSubQuads = kHistMaxParticles / 4;
 constexpr long long kMaxSlots = 1LL << 29;            // particle slots per handle
 constexpr int kDeadSmem = 8192;                       // absorbed slots staged in k_post
 constexpr int kTwo24 = 1 << 24;
@@ -132,10 +136,20 @@ struct DevState {
   int64_t* prof;           // [3][tn] sum of sampled species deposits, 2^24 units per particle
   int64_t* prof_n;         // [n_inst] samples taken
   int wait_limit;          // polls of a push-kernel bulk-copy wait before PIC_ETIMEOUT
+  int* bw;                 // [G] push-block weights: each block's share of the particles
+  long long* bwp;          // [G + 1] their prefix sums (the block ranges are Q bwp[b] / bwp[G])
+  int* bt;                 // [G] streaming time of each block in the last push, ns
+  int agg;
 };
 
 // Is the state after step n a profile sample?  (Sec. 3 late-time averages:
 // steps n >= window_start with (n - window_start) a multiple of the period.)
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 __device__ __forceinline__ bool profile_due(long long period, long long window_start, long long n) {
   return period > 0 && n >= window_start && (n - window_start) % period == 0;
 }
@@ -235,6 +249,55 @@ __device__ __forceinline__ void cell_of(float z, float inv_dz, int Nz, int& j, f
   j = (int)jj;
   const float jf = fminf(__fsub_rn(t, 12582912.0f), (float)(Nz - 1));
   f = __fsub_rn(s, jf);
+}
+
+// Two FP32 values per instruction (the f32x2 forms of sm_100 and later):
+// each element is rounded exactly like the scalar operation of the same
+// rounding mode, so pairs give the scalar results bit for bit.
+__device__ __forceinline__ unsigned long long f2_bits(float a, float b) {
+  return ((unsigned long long)__float_as_uint(b) << 32) | (unsigned long long)__float_as_uint(a);
+}
+__device__ __forceinline__ void f2_split(unsigned long long u, float& a, float& b) {
+  a = __uint_as_float((unsigned)u);
+  b = __uint_as_float((unsigned)(u >> 32));
+}
+__device__ __forceinline__ unsigned long long mul2_rn(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long add2_rz(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long sub2_rn(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long fma2_rn(unsigned long long a, unsigned long long b,
+                                                      unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// cell_of for two positions at once (same rule, same results)
+__device__ __forceinline__ void cell_of2(float z0, float z1, float inv_dz, int Nz, int& j0,
+                                         int& j1, float& f0, float& f1) {
+  const unsigned long long s = mul2_rn(f2_bits(z0, z1), f2_bits(inv_dz, inv_dz));
+  const unsigned long long t = add2_rz(s, f2_bits(12582912.0f, 12582912.0f));
+  const unsigned long long tj = sub2_rn(t, f2_bits(12582912.0f, 12582912.0f));
+  float t0, t1, a0, a1;
+  f2_split(t, t0, t1);
+  f2_split(tj, a0, a1);
+  const unsigned top = (unsigned)(Nz - 1);
+  j0 = (int)min((unsigned)(__float_as_int(t0) - 0x4B400000), top);
+  j1 = (int)min((unsigned)(__float_as_int(t1) - 0x4B400000), top);
+  const float ftop = (float)(Nz - 1);
+  const unsigned long long f = sub2_rn(s, f2_bits(fminf(a0, ftop), fminf(a1, ftop)));
+  f2_split(f, f0, f1);
 }
 
 // Q = trunc(f 2^24): f in [0, 1] makes the product exact and below 2^32, so a

@@ -39,12 +39,9 @@ __device__ void seg_quad_prefix(const DevState& st, long long* segS, long long* 
   __syncthreads();
 }
 
-// blocks that get work: at least one quad per thread, and no block above
-// kPushMaxParticlesPerBlock particles (the host sizes the grid for that)
+// blocks that get work: at least one quad per thread
 __device__ __forceinline__ int effective_blocks(long long Q, int grid, int threads) {
   long long need = (Q + threads - 1) / threads;
-  const long long cap_need = (4 * Q + kPushMaxParticlesPerBlock - 1) / kPushMaxParticlesPerBlock;
-  if (need < cap_need) need = cap_need;
   if (need < 1) need = 1;
   return (int)(need < grid ? need : grid);
 }
@@ -57,33 +54,28 @@ __device__ __forceinline__ long long warp_start(long long q0, long long q1, int 
 
 // ------------------------------------------------------------------ deposit
 // Per-block charge histogram in shared memory with native 32-bit atomics.
-// For cell j it keeps the particle count and the sum of the fixed-point
-// fractions Q = Qh 2^12 + Ql split in two 12-bit halves, so no counter can
-// overflow before 2^20 particles have landed in one cell.  Node j's charge
-// is then sign * (cnt_j 2^24 - Qs_j + Qs_{j-1}), Qs = sum Q -- exactly the
+// For cell j it keeps three counters side by side (one address, offsets 0,
+// 4, 8): the particle count and the sum of the fixed-point fractions Q = Qh
+// 2^12 + Ql split in two 12-bit halves, so no counter can overflow: a block
+// bins fewer than 2^20 particles (kHistMaxParticles).  Node j's charge is
+// then sign * (cnt_j 2^24 - Qs_j + Qs_{j-1}), Qs = sum Q -- exactly the
 // linear-weight rule, in 64-bit integers at flush time.
 struct Hist {
-  unsigned* cnt;
-  unsigned* qh;
-  unsigned* ql;
+  unsigned* h3;              // [cell][count, Qh sum, Ql sum]
 };
 
 __device__ __forceinline__ void hist_zero(const Hist& h, int n_cells) {
-  for (int j = threadIdx.x; j < n_cells; j += blockDim.x) {
-    h.cnt[j] = 0u;
-    h.qh[j] = 0u;
-    h.ql[j] = 0u;
-  }
+  for (int j = threadIdx.x; j < 3 * n_cells; j += blockDim.x) h.h3[j] = 0u;
 }
 
 __device__ __forceinline__ long long qsum(const Hist& h, int j) {
-  return (long long)h.qh[j] * 4096 + (long long)h.ql[j];
+  return (long long)h.h3[3 * j + 1] * 4096 + (long long)h.h3[3 * j + 2];
 }
 
 // node charge of cells j-1 and j; callers sync before and after
 __device__ __forceinline__ long long hist_node(const Hist& h, int j, int Nz) {
   long long v = 0;
-  if (j < Nz) v += (long long)h.cnt[j] * kTwo24 - qsum(h, j);
+  if (j < Nz) v += (long long)h.h3[3 * j] * kTwo24 - qsum(h, j);
   if (j > 0) v += qsum(h, j - 1);
   return v;
 }
@@ -95,78 +87,86 @@ __device__ __forceinline__ void hist_flush(const Hist& h, int Nz, long long sgn,
   }
 }
 
-__device__ __forceinline__ void hist_add(const Hist& h, int j, int q) {
-  atomicAdd(&h.cnt[j], 1u);
-  atomicAdd(&h.qh[j], (unsigned)(q >> 12));
-  atomicAdd(&h.ql[j], (unsigned)(q & 4095));
-}
-
-__device__ __forceinline__ void hist_deposit(const Hist& h, float z, float inv_dz, int Nz) {
-  int j;
-  float f;
-  cell_of(z, inv_dz, Nz, j, f);
-  hist_add(h, j, (int)frac_units(f));
+__device__ __forceinline__ void hist_add(const Hist& h, int j, unsigned q) {
+  unsigned* c = h.h3 + 3 * j;
+  atomicAdd(c, 1u);
+  atomicAdd(c + 1, q >> 12);
+  atomicAdd(c + 2, q & 4095u);
 }
 
 // Deposit up to 4 particles per lane (bit k of am: z[k] is deposited).
-// Called by all 32 lanes.  When the warp's cells span fewer than 4 cells the
-// lanes bin in registers and the warp adds 12 totals; otherwise one set of
-// atomics per particle.
+// Called by all 32 lanes.  With agg set and the warp's cells spanning fewer
+// than 4 cells (a state sorted by cell), the lanes bin in registers and the
+// warp adds 12 totals; otherwise one set of atomics per particle.
 __device__ __forceinline__ void deposit_warp(const Hist& h, const float (&z)[4], unsigned am,
-                                             float inv_dz, int Nz) {
-  int j[4], q[4];
+                                             float inv_dz, int Nz, bool agg) {
+  int j[4];
+  unsigned q[4];
   int jlo = 0x7fffffff, jhi = -1;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     j[k] = 0;
-    q[k] = 0;
+    q[k] = 0u;
     if (am & (1u << k)) {
       float f;
       cell_of(z[k], inv_dz, Nz, j[k], f);
-      q[k] = (int)frac_units(f);
+      q[k] = frac_units(f);
       jlo = min(jlo, j[k]);
       jhi = max(jhi, j[k]);
     }
   }
-  const int wlo = __reduce_min_sync(0xffffffffu, jlo);
-  const int whi = __reduce_max_sync(0xffffffffu, jhi);
-  if (whi < 0) return;                        // nothing to deposit in this warp
-  if (whi - wlo < 4) {
-    unsigned c[4] = {0u, 0u, 0u, 0u}, hh[4] = {0u, 0u, 0u, 0u}, ll[4] = {0u, 0u, 0u, 0u};
+  if (agg) {
+    const int wlo = __reduce_min_sync(0xffffffffu, jlo);
+    const int whi = __reduce_max_sync(0xffffffffu, jhi);
+    if (whi < 0) return;                        // nothing to deposit in this warp
+    if (whi - wlo < 4) {
+      unsigned c[4] = {0u, 0u, 0u, 0u}, hh[4] = {0u, 0u, 0u, 0u}, ll[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (am & (1u << k)) {
-        const int b = j[k] - wlo;
-        const unsigned qh = (unsigned)(q[k] >> 12), ql = (unsigned)(q[k] & 4095);
+      for (int k = 0; k < 4; ++k) {
+        if (am & (1u << k)) {
+          const int b = j[k] - wlo;
+          const unsigned qh = q[k] >> 12, ql = q[k] & 4095u;
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          c[t] += (b == t) ? 1u : 0u;
-          hh[t] += (b == t) ? qh : 0u;
-          ll[t] += (b == t) ? ql : 0u;
+          for (int t = 0; t < 4; ++t) {
+            c[t] += (b == t) ? 1u : 0u;
+            hh[t] += (b == t) ? qh : 0u;
+            ll[t] += (b == t) ? ql : 0u;
+          }
         }
       }
-    }
-    const int lane = threadIdx.x & 31;
-    unsigned mine = 0u;
+      const int lane = threadIdx.x & 31;
+      unsigned mine = 0u;
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const unsigned sc = __reduce_add_sync(0xffffffffu, c[t]);
-      const unsigned sh = __reduce_add_sync(0xffffffffu, hh[t]);
-      const unsigned sl = __reduce_add_sync(0xffffffffu, ll[t]);
-      if (lane == t) mine = sc;
-      if (lane == 4 + t) mine = sh;
-      if (lane == 8 + t) mine = sl;
+      for (int t = 0; t < 4; ++t) {
+        const unsigned sc = __reduce_add_sync(0xffffffffu, c[t]);
+        const unsigned sh = __reduce_add_sync(0xffffffffu, hh[t]);
+        const unsigned sl = __reduce_add_sync(0xffffffffu, ll[t]);
+        if (lane == t) mine = sc;
+        if (lane == 4 + t) mine = sh;
+        if (lane == 8 + t) mine = sl;
+      }
+      // lane 4 w + t adds word w of cell wlo + t
+      if (lane < 12 && mine != 0u) atomicAdd(h.h3 + 3 * (wlo + (lane & 3)) + (lane >> 2), mine);
+      return;
     }
-    if (lane < 12 && mine != 0u) {
-      const int cell = wlo + (lane & 3);
-      unsigned* arr = lane < 4 ? h.cnt : (lane < 8 ? h.qh : h.ql);
-      atomicAdd(&arr[cell], mine);
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (am & (1u << k)) hist_add(h, j[k], q[k]);
   }
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (am & (1u << k)) hist_add(h, j[k], q[k]);
+}
+
+// Deposit all four particles of every lane (none absorbed, no aggregation):
+// straight-line code, the cell rule taken two particles at a time.
+__device__ __forceinline__ void deposit_quad(const Hist& h, const float4& z4, float inv_dz,
+                                             int Nz) {
+  int j0, j1, j2, j3;
+  float f0, f1, f2, f3;
+  cell_of2(z4.x, z4.y, inv_dz, Nz, j0, j1, f0, f1);
+  cell_of2(z4.z, z4.w, inv_dz, Nz, j2, j3, f2, f3);
+  hist_add(h, j0, frac_units(f0));
+  hist_add(h, j1, frac_units(f1));
+  hist_add(h, j2, frac_units(f2));
+  hist_add(h, j3, frac_units(f3));
 }
 
 // ------------------------------------------------------------------ MCC
@@ -344,16 +344,27 @@ __device__ __forceinline__ void push_quad(const SegCtx& c, const float2* Es2, fl
   float v[4] = {v4.x, v4.y, v4.z, v4.w};
   const uint32_t id[4] = {id4.x, id4.y, id4.z, id4.w};
   unsigned d = 0u;
+  int j[4];
+  float f[4];
+  cell_of2(z[0], z[1], c.inv_dz, c.Nz, j[0], j[1], f[0], f[1]);
+  cell_of2(z[2], z[3], c.inv_dz, c.Nz, j[2], j[3], f[2], f[3]);
+  float Ez[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    int j;
-    float f;
-    cell_of(z[k], c.inv_dz, c.Nz, j, f);
-    const float2 e = Es2[j];
-    v[k] = fmaf(c.qmdt, fmaf(f, e.y, e.x), v[k]);
-    z[k] = fmaf(v[k], c.dt, z[k]);
-    d |= (z[k] >= 0.0f && z[k] < c.Lf) ? 0u : (1u << k);
+    const float2 e = Es2[j[k]];
+    Ez[k] = fmaf(f[k], e.y, e.x);
   }
+  // v += (q/m dt) E, z += v dt, two particles per instruction
+  const unsigned long long qm2 = f2_bits(c.qmdt, c.qmdt), dt2 = f2_bits(c.dt, c.dt);
+#pragma unroll
+  for (int k = 0; k < 4; k += 2) {
+    const unsigned long long v2 = fma2_rn(qm2, f2_bits(Ez[k], Ez[k + 1]), f2_bits(v[k], v[k + 1]));
+    const unsigned long long z2 = fma2_rn(v2, dt2, f2_bits(z[k], z[k + 1]));
+    f2_split(v2, v[k], v[k + 1]);
+    f2_split(z2, z[k], z[k + 1]);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) d |= (z[k] >= 0.0f && z[k] < c.Lf) ? 0u : (1u << k);
   unsigned m = 0u;
   if (c.tc != 0u) {                      // uniform over the segment
     uint32_t a[4], b[4];
@@ -387,9 +398,7 @@ __device__ __forceinline__ void push_body(const DevState& st) {
   const int mn = st.max_nodes;
   float2* Es2 = reinterpret_cast<float2*>(smem);
   Hist hist;
-  hist.cnt = reinterpret_cast<unsigned*>(smem + (size_t)mn * 8);
-  hist.qh = hist.cnt + mn;
-  hist.ql = hist.qh + mn;
+  hist.h3 = reinterpret_cast<unsigned*>(smem + (size_t)mn * 8);
   long long* segS = reinterpret_cast<long long*>(smem + (size_t)mn * 20 + ((mn & 1) ? 4 : 0));
   // per-warp double-buffered staging of (z, v_z, id) chunks and their mbarriers
   const size_t stage_off = ((size_t)mn * 20 + 8 + (size_t)(st.n_seg + 1) * 8 + 127) & ~(size_t)127;
@@ -413,15 +422,31 @@ __device__ __forceinline__ void push_body(const DevState& st) {
     if (threadIdx.x == 0) st.part[st.n_seg + 1] = Geff;
   }
   if ((int)blockIdx.x >= Geff) return;
-  const long long lo = (long long)blockIdx.x * Q / Geff;
-  const long long hi = ((long long)blockIdx.x + 1) * Q / Geff;
+  long long lo, hi;
+  if (kDepositOnly) {
+    lo = (long long)blockIdx.x * Q / Geff;
+    hi = ((long long)blockIdx.x + 1) * Q / Geff;
+  } else {
+    // the block's share of the quads is its weight (integer, set from each
+    // block's throughput in the last push, so that SMs that stream slower
+    // get less and all blocks finish together); the ranges come from exact
+    // integer prefix sums of the weights, so they tile [0, Q) exactly.  The
+    // prefix is over the launched blocks; blocks past G_eff share nothing.
+    const long long* wp = st.bwp;
+    const long long tot = wp[Geff];
+    lo = Q * wp[blockIdx.x] / tot;
+    hi = Q * wp[blockIdx.x + 1] / tot;
+  }
   if (!kDepositOnly && threadIdx.x == 0) {
     // the block ranges, for the post kernel (which would otherwise redo
     // G_eff 64-bit divisions on one SM)
     st.bstart[blockIdx.x] = lo;
     if ((int)blockIdx.x == Geff - 1) st.bstart[Geff] = hi;
   }
-  if (lo >= hi) return;
+  if (lo >= hi) {
+    if (!kDepositOnly && threadIdx.x == 0) st.bt[blockIdx.x] = 0;
+    return;
+  }
   const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   // first segment whose quad range ends after lo
@@ -435,6 +460,7 @@ __device__ __forceinline__ void push_body(const DevState& st) {
   unsigned phase = 0u;                 // parity of this warp's two stage barriers
   unsigned char* wstage = stages + (size_t)warp * 2 * kStageBytes;
   unsigned long long* wbar = bars + 2 * warp;
+  const unsigned long long t_start = global_ns();
   for (int g = glo; g < st.n_seg && segS[g] < hi; ++g) {
     const long long s0 = segS[g], s1 = segS[g + 1];
     if (s1 <= lo || s1 == s0) continue;
@@ -457,175 +483,190 @@ __device__ __forceinline__ void push_body(const DevState& st) {
       }
       cur = inst;
     }
-    hist_zero(hist, icS.Nz);
-    __syncthreads();
-    // quads of this block and warp, relative to the segment: 32-bit (a
-    // segment holds < 2^31 particles)
+    // quads of this block, relative to the segment: 32-bit (a segment holds
+    // < 2^31 particles); taken kSubQuads at a time, each sub-range binned
+    // and flushed on its own so that no counter of the histogram overflows
     const int q0 = (int)((lo > s0 ? lo : s0) - s0);
     const int q1 = (int)((hi < s1 ? hi : s1) - s0);
-    const int wq0 = (int)warp_start(q0, q1, warp, W), wq1 = (int)warp_start(q0, q1, warp + 1, W);
-    const long long off = st.seg_off[g];
-    const int N = st.seg_count[g];
-    float* __restrict__ zp = st.z + off;
-    float* __restrict__ vzp = st.vz + off;
-    const uint32_t* __restrict__ idp = st.id + off;
-    const float inv_dz = icS.inv_dz_f;
-    const int Nz = icS.Nz;
+    int dead_total = 0;                // absorbed slots the block listed for this segment
+    for (int a = q0; a < q1; a += kSubQuads) {
+      const int b1 = (q1 - a > kSubQuads) ? a + kSubQuads : q1;
+      hist_zero(hist, icS.Nz);
+      __syncthreads();
+      const int wq0 = (int)warp_start(a, b1, warp, W), wq1 = (int)warp_start(a, b1, warp + 1, W);
+      const long long off = st.seg_off[g];
+      const int N = st.seg_count[g];
+      float* __restrict__ zp = st.z + off;
+      float* __restrict__ vzp = st.vz + off;
+      const uint32_t* __restrict__ idp = st.id + off;
+      const float inv_dz = icS.inv_dz_f;
+      const int Nz = icS.Nz;
+      const bool agg = st.agg != 0;
 
-    SegCtx c;
-    c.inv_dz = inv_dz;
-    c.Lf = icS.L_f;
-    c.dt = icS.dt_f;
-    c.qmdt = icS.qmdt[sp];
-    c.Nz = Nz;
-    c.tc = icS.t_cand[sp];
-    c.ck = icS.ckey[sp];
-    c.stepw = kDepositOnly ? 0u : (uint32_t)st.dyn[inst].step;
-#pragma unroll
-    for (int r = 0; r < 10; ++r) c.rk[r] = c.ck + (uint32_t)r * 0x9E3779B9u;
-    uint32_t* dbuf = st.dead_buf + off + 4 * wq0;
-    int dead_run = 0;
+      SegCtx c;
+      c.inv_dz = inv_dz;
+      c.Lf = icS.L_f;
+      c.dt = icS.dt_f;
+      c.qmdt = icS.qmdt[sp];
+      c.Nz = Nz;
+      c.tc = icS.t_cand[sp];
+      c.ck = icS.ckey[sp];
+      c.stepw = kDepositOnly ? 0u : (uint32_t)st.dyn[inst].step;
+  #pragma unroll
+      for (int r = 0; r < 10; ++r) c.rk[r] = c.ck + (uint32_t)r * 0x9E3779B9u;
+      uint32_t* dbuf = st.dead_buf + off + 4 * wq0;
+      int dead_run = 0;
 
-    // chunk ch of this warp = quads [wq0 + 32 ch, +32); bulk copies run two
-    // chunks ahead of the compute
-    const int nchunks = (int)((wq1 - wq0 + 31) >> 5);
-    auto issue = [&](int ch) {
-      const int s = ch & 1;
-      const int qc = wq0 + 32 * ch;
-      const int nq = (wq1 - qc) < 32 ? (wq1 - qc) : 32;
-      const uint32_t bytes = (uint32_t)nq * 16u;
-      unsigned char* b = wstage + s * kStageBytes;
-      fence_proxy_async();
-      mbar_expect_tx(&wbar[s], 3u * bytes);
-      bulk_g2s(b, zp + 4 * qc, bytes, &wbar[s]);
-      bulk_g2s(b + 512, vzp + 4 * qc, bytes, &wbar[s]);
-      bulk_g2s(b + 1024, idp + 4 * qc, bytes, &wbar[s]);
-    };
-    if (!kDepositOnly && lane == 0) {
-      if (nchunks > 0) issue(0);
-      if (nchunks > 1) issue(1);
-    }
-    int ch = 0;
-    for (int base = wq0; base < wq1; base += 32, ++ch) {
-      const int q = base + lane;
-      unsigned dm = 0, cm = 0, am = 0;
-      float zz[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-      float4 z4s = make_float4(0.f, 0.f, 0.f, 0.f), v4s = z4s;
-      uint4 id4s = make_uint4(0u, 0u, 0u, 0u);
-      if (!kDepositOnly) {
+      // chunk ch of this warp = quads [wq0 + 32 ch, +32); bulk copies run two
+      // chunks ahead of the compute
+      const int nchunks = (int)((wq1 - wq0 + 31) >> 5);
+      auto issue = [&](int ch) {
         const int s = ch & 1;
-        const bool arrived = mbar_wait_bounded(&wbar[s], (phase >> s) & 1u, st.wait_limit);
-        if (!__all_sync(0xffffffffu, arrived)) {
-          // the copy did not complete in time: flag it, let this warp's copies
-          // in flight (this stage and the next) land with the full limit, keep
-          // the stage parities in step, and stop this warp's part of the segment
-          if (lane == 0) atomicOr(&st.dyn[inst].err, ERR_TIMEOUT);
-          if (mbar_wait_bounded(&wbar[s], (phase >> s) & 1u)) phase ^= 1u << s;
-          if (ch + 1 < nchunks && mbar_wait_bounded(&wbar[s ^ 1], (phase >> (s ^ 1)) & 1u))
-            phase ^= 1u << (s ^ 1);
-          break;
-        }
-        phase ^= 1u << s;
-        const unsigned char* b = wstage + s * kStageBytes;
-        if (q < wq1) {
-          z4s = reinterpret_cast<const float4*>(b)[lane];
-          v4s = reinterpret_cast<const float4*>(b + 512)[lane];
-          id4s = reinterpret_cast<const uint4*>(b + 1024)[lane];
-        }
-        __syncwarp();
-        if (lane == 0 && ch + 2 < nchunks) issue(ch + 2);
+        const int qc = wq0 + 32 * ch;
+        const int nq = (wq1 - qc) < 32 ? (wq1 - qc) : 32;
+        const uint32_t bytes = (uint32_t)nq * 16u;
+        unsigned char* b = wstage + s * kStageBytes;
+        fence_proxy_async();
+        mbar_expect_tx(&wbar[s], 3u * bytes);
+        bulk_g2s(b, zp + 4 * qc, bytes, &wbar[s]);
+        bulk_g2s(b + 512, vzp + 4 * qc, bytes, &wbar[s]);
+        bulk_g2s(b + 1024, idp + 4 * qc, bytes, &wbar[s]);
+      };
+      if (!kDepositOnly && lane == 0) {
+        if (nchunks > 0) issue(0);
+        if (nchunks > 1) issue(1);
       }
-      if (q < wq1) {
-        const int i = 4 * q;
-        if (i + 3 < N) {
+      int ch = 0;
+      for (int base = wq0; base < wq1; base += 32, ++ch) {
+        const int q = base + lane;
+        unsigned dm = 0, cm = 0, am = 0;
+        float zz[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        float4 z4s = make_float4(0.f, 0.f, 0.f, 0.f), v4s = z4s;
+        uint4 id4s = make_uint4(0u, 0u, 0u, 0u);
+        if (!kDepositOnly) {
+          const int s = ch & 1;
+          const bool arrived = mbar_wait_bounded(&wbar[s], (phase >> s) & 1u, st.wait_limit);
+          if (!__all_sync(0xffffffffu, arrived)) {
+            // the copy did not complete in time: flag it, let this warp's copies
+            // in flight (this stage and the next) land with the full limit, keep
+            // the stage parities in step, and stop this warp's part of the segment
+            if (lane == 0) atomicOr(&st.dyn[inst].err, ERR_TIMEOUT);
+            if (mbar_wait_bounded(&wbar[s], (phase >> s) & 1u)) phase ^= 1u << s;
+            if (ch + 1 < nchunks && mbar_wait_bounded(&wbar[s ^ 1], (phase >> (s ^ 1)) & 1u))
+              phase ^= 1u << (s ^ 1);
+            break;
+          }
+          phase ^= 1u << s;
+          const unsigned char* b = wstage + s * kStageBytes;
+          if (q < wq1) {
+            z4s = reinterpret_cast<const float4*>(b)[lane];
+            v4s = reinterpret_cast<const float4*>(b + 512)[lane];
+            id4s = reinterpret_cast<const uint4*>(b + 1024)[lane];
+          }
+          __syncwarp();
+          if (lane == 0 && ch + 2 < nchunks) issue(ch + 2);
+        }
+        if (base + 32 <= wq1 && 4 * (base + 32) <= N) {
+          // every lane holds four live particles (warp-uniform): straight-line
+          // push and, unless one of the warp's particles left the gap or the
+          // state is sorted, straight-line deposit
+          const int i = 4 * q;
           float4 z4 = kDepositOnly ? __ldcs(reinterpret_cast<const float4*>(zp + i)) : z4s;
-          if (kDepositOnly) {
-            am = 0xFu;
-          } else {
+          if (!kDepositOnly) {
             float4 v4 = v4s;
             push_quad(c, Es2, z4, v4, id4s, dm, cm);
-            am = ~dm & 0xFu;
             __stcs(reinterpret_cast<float4*>(zp + i), z4);
             __stcs(reinterpret_cast<float4*>(vzp + i), v4);
           }
-          zz[0] = z4.x; zz[1] = z4.y; zz[2] = z4.z; zz[3] = z4.w;
+          if (!agg && !__any_sync(0xffffffffu, dm != 0u)) {
+            deposit_quad(hist, z4, inv_dz, Nz);
+          } else {
+            zz[0] = z4.x; zz[1] = z4.y; zz[2] = z4.z; zz[3] = z4.w;
+            deposit_warp(hist, zz, ~dm & 0xFu, inv_dz, Nz, agg);
+          }
         } else {
-          const float zq[4] = {z4s.x, z4s.y, z4s.z, z4s.w};
-          const float vq[4] = {v4s.x, v4s.y, v4s.z, v4s.w};
-          const uint32_t iq[4] = {id4s.x, id4s.y, id4s.z, id4s.w};
-          for (int k2 = 0; k2 < 4; ++k2) {
-            if (i + k2 < N) {
-              float zv = kDepositOnly ? zp[i + k2] : zq[k2];
-              if (!kDepositOnly) {
-                float vv = vq[k2];
-                const unsigned r = push_one(c, Es2, zv, vv, iq[k2]);
-                if (r & 1u) dm |= 1u << k2;
-                if (r & 2u) cm |= 1u << k2;
-                zp[i + k2] = zv;
-                vzp[i + k2] = vv;
-              }
-              if (!(dm & (1u << k2))) {
-                zz[k2] = zv;
-                am |= 1u << k2;
+          if (q < wq1) {
+            const int i = 4 * q;
+            const float zq[4] = {z4s.x, z4s.y, z4s.z, z4s.w};
+            const float vq[4] = {v4s.x, v4s.y, v4s.z, v4s.w};
+            const uint32_t iq[4] = {id4s.x, id4s.y, id4s.z, id4s.w};
+            for (int k2 = 0; k2 < 4; ++k2) {
+              if (i + k2 < N) {
+                float zv = kDepositOnly ? zp[i + k2] : zq[k2];
+                if (!kDepositOnly) {
+                  float vv = vq[k2];
+                  const unsigned r = push_one(c, Es2, zv, vv, iq[k2]);
+                  if (r & 1u) dm |= 1u << k2;
+                  if (r & 2u) cm |= 1u << k2;
+                  zp[i + k2] = zv;
+                  vzp[i + k2] = vv;
+                }
+                if (!(dm & (1u << k2))) {
+                  zz[k2] = zv;
+                  am |= 1u << k2;
+                }
               }
             }
           }
+          deposit_warp(hist, zz, am, inv_dz, Nz, agg);
         }
-      }
-      deposit_warp(hist, zz, am, inv_dz, Nz);
-      if (kDepositOnly) continue;
-      // collision candidates -> compact list; absorbed slots -> this warp's
-      // ordered list (warp scans, one atomic per warp with candidates); most
-      // iterations have neither
-      if (!__any_sync(0xffffffffu, (cm | dm) != 0u)) continue;
-      const int cc = __popc(cm), dc = __popc(dm);
-      int ci = cc, di = dc;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int yc = __shfl_up_sync(0xffffffffu, ci, o);
-        const int yd = __shfl_up_sync(0xffffffffu, di, o);
-        if (lane >= o) { ci += yc; di += yd; }
-      }
-      const int ctot = __shfl_sync(0xffffffffu, ci, 31);
-      const int dtot = __shfl_sync(0xffffffffu, di, 31);
-      if (ctot) {
-        unsigned cbase = 0;
-        if (lane == 0) cbase = atomicAdd(st.cand_count, (unsigned)ctot);
-        cbase = __shfl_sync(0xffffffffu, cbase, 0);
-        unsigned w = cbase + (unsigned)(ci - cc);
-        for (int k2 = 0; k2 < 4; ++k2) {
-          if (cm & (1u << k2)) {
-            if (w < (unsigned)st.cand_cap)
-              st.cand_buf[w] = ((unsigned long long)g << 32) | (unsigned long long)(4 * q + k2);
-            else
-              atomicOr(&st.dyn[inst].err, ERR_CAPACITY);
-            ++w;
+        if (kDepositOnly) continue;
+        // collision candidates -> compact list; absorbed slots -> this warp's
+        // ordered list (warp scans, one atomic per warp with candidates); most
+        // iterations have neither
+        if (!__any_sync(0xffffffffu, (cm | dm) != 0u)) continue;
+        const int cc = __popc(cm), dc = __popc(dm);
+        int ci = cc, di = dc;
+  #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int yc = __shfl_up_sync(0xffffffffu, ci, o);
+          const int yd = __shfl_up_sync(0xffffffffu, di, o);
+          if (lane >= o) { ci += yc; di += yd; }
+        }
+        const int ctot = __shfl_sync(0xffffffffu, ci, 31);
+        const int dtot = __shfl_sync(0xffffffffu, di, 31);
+        if (ctot) {
+          unsigned cbase = 0;
+          if (lane == 0) cbase = atomicAdd(st.cand_count, (unsigned)ctot);
+          cbase = __shfl_sync(0xffffffffu, cbase, 0);
+          unsigned w = cbase + (unsigned)(ci - cc);
+          for (int k2 = 0; k2 < 4; ++k2) {
+            if (cm & (1u << k2)) {
+              if (w < (unsigned)st.cand_cap)
+                st.cand_buf[w] = ((unsigned long long)g << 32) | (unsigned long long)(4 * q + k2);
+              else
+                atomicOr(&st.dyn[inst].err, ERR_CAPACITY);
+              ++w;
+            }
           }
         }
+        if (dtot) {
+          int w = dead_run + di - dc;
+          for (int k2 = 0; k2 < 4; ++k2)
+            if (dm & (1u << k2)) dbuf[w++] = (uint32_t)(4 * q + k2);
+          dead_run += dtot;
+        }
       }
-      if (dtot) {
-        int w = dead_run + di - dc;
-        for (int k2 = 0; k2 < 4; ++k2)
-          if (dm & (1u << k2)) dbuf[w++] = (uint32_t)(4 * q + k2);
-        dead_run += dtot;
+      // concatenate the warps' ordered lists into one list per block
+      if (!kDepositOnly) {
+        if (lane == 0) wcount[warp] = dead_run;
+        __syncthreads();
+        int start = 0, total = 0;
+        for (int w = 0; w < W; ++w) {
+          if (w < warp) start += wcount[w];
+          total += wcount[w];
+        }
+        uint32_t* dst = st.dead_dense + off + 4 * q0 + dead_total + start;
+        for (int k2 = lane; k2 < dead_run; k2 += 32) dst[k2] = dbuf[k2];
+        dead_total += total;
+        if (threadIdx.x == 0) st.dcount[(long long)g * st.G + blockIdx.x] = dead_total;
       }
-    }
-    // concatenate the warps' ordered lists into one list per block
-    if (!kDepositOnly) {
-      if (lane == 0) wcount[warp] = dead_run;
       __syncthreads();
-      int start = 0, total = 0;
-      for (int w = 0; w < W; ++w) {
-        if (w < warp) start += wcount[w];
-        total += wcount[w];
-      }
-      uint32_t* dst = st.dead_dense + off + 4 * q0 + start;
-      for (int k2 = lane; k2 < dead_run; k2 += 32) dst[k2] = dbuf[k2];
-      if (threadIdx.x == 0) st.dcount[(long long)g * st.G + blockIdx.x] = total;
+      hist_flush(hist, Nz, sgn, st.rho_acc + icS.node_off);
     }
-    __syncthreads();
-    hist_flush(hist, Nz, sgn, st.rho_acc + icS.node_off);
   }
+  if (!kDepositOnly && threadIdx.x == 0)
+    st.bt[blockIdx.x] = (int)min(global_ns() - t_start, 2000000000ull);
 }
 
 __global__ void __launch_bounds__(384, 2) k_push(DevState st) { push_body<false>(st); }
@@ -728,6 +769,46 @@ __global__ void __launch_bounds__(kPostThreads) k_phi(DevState st) {
   for (int j = threadIdx.x; j < nn; j += blockDim.x) rho_s[j] = st.rho[off + j];
   __syncthreads();
   field_solve(ic, rho_s, st.E + off, st.phi + off, ws64);
+}
+
+// ------------------------------------------------------------------ weights
+// New push-block weights from the last push: block b streamed its share w_b
+// in t_b ns, so its rate is w_b / t_b; the next shares follow the rates
+// (relative to their mean), halfway from the old weights, within
+// [kMinWeight, kMaxWeight].  Blocks without a time keep their weight.  Then
+// the prefix sums over all launched blocks.  One block does it; every block
+// of the next push reads the result.
+__device__ void update_push_weights(const DevState& st, int G, float* ws, long long* ws64) {
+  float r_sum = 0.0f, n = 0.0f;
+  for (int b = threadIdx.x; b < G; b += blockDim.x) {
+    const int t = st.bt[b];
+    if (t > 0) {
+      r_sum += (float)st.bw[b] / (float)t;
+      n += 1.0f;
+    }
+  }
+  r_sum = block_sum<float>(r_sum, ws);
+  n = block_sum<float>(n, ws);
+  if (n <= 0.0f || !(r_sum > 0.0f)) return;
+  const float mean = r_sum / n;
+  for (int b = threadIdx.x; b < G; b += blockDim.x) {
+    const int t = st.bt[b];
+    if (t <= 0) continue;
+    const float target = (float)kNominalWeight * ((float)st.bw[b] / (float)t) / mean;
+    const float w = 0.5f * ((float)st.bw[b] + target);
+    st.bw[b] = (int)fminf(fmaxf(rintf(w), (float)kMinWeight), (float)kMaxWeight);
+  }
+  __syncthreads();
+  long long carry = 0;
+  for (int base = 0; base < st.G; base += blockDim.x) {
+    const int b = base + threadIdx.x;
+    const long long w = b < st.G ? (long long)st.bw[b] : 0LL;
+    long long tot;
+    const long long ex = block_exclusive_scan<long long>(w, &tot, ws64);
+    if (b < st.G) st.bwp[b + 1] = carry + ex + w;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) st.bwp[0] = 0;
 }
 
 // ------------------------------------------------------------------ k_post
@@ -875,7 +956,6 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post(DevState st) {
   __syncthreads();                 // ic is read by every thread below
   InstDyn* dyn = st.dyn + inst;
   PostScratch* ps = st.post + inst;
-  const long long Q = st.part[st.n_seg];
   const int Geff = (int)st.part[st.n_seg + 1];
   const long long step = dyn->step;
   const uint32_t base_id = dyn->next_id;
@@ -1070,6 +1150,9 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post(DevState st) {
     newN = min(Nn + E + P, cap);
   }
   if (__syncthreads_or(overflow) && tid == 0) atomicOr(&dyn->err, ERR_CAPACITY);
+  // the plasma-electron block of diode 0 (usually the lightest) re-weights
+  // the push blocks for the next step
+  if ((int)blockIdx.x == 1) update_push_weights(st, Geff, reinterpret_cast<float*>(wsd2), ws64);
 
   // every thread's moves, appends and charge are complete and visible before
   // the arrival
@@ -1168,8 +1251,7 @@ __global__ void __launch_bounds__(256) k_profile(DevState st) {
   const InstConst& ic = st.ic[inst];
   if (!profile_due(st.prof_period, ic.window_start, st.dyn[inst].step - 1)) return;
   const int Nz = ic.Nz;
-  unsigned* hb = reinterpret_cast<unsigned*>(smem);
-  const Hist h{hb, hb + Nz, hb + 2 * Nz};
+  const Hist h{reinterpret_cast<unsigned*>(smem)};
   hist_zero(h, Nz);
   __syncthreads();
   const int n = st.seg_count[g];
@@ -1183,7 +1265,7 @@ __global__ void __launch_bounds__(256) k_profile(DevState st) {
       zz[0] = zs[i];
       am = 1u;
     }
-    deposit_warp(h, zz, am, inv, Nz);
+    deposit_warp(h, zz, am, inv, Nz, true);
   }
   __syncthreads();
   hist_flush(h, Nz, 1LL, st.prof + (long long)sp * st.tn + ic.node_off);
