@@ -163,8 +163,9 @@ typedef struct pic_diag {
 typedef struct pic_profile {
     int64_t steps;
     double ms_push;               /* gather+push+absorb+candidate test+deposit kernel */
-    double ms_mcc;                /* collisions of the step's candidates */
-    double ms_post;               /* compaction+injection+field solve kernel */
+    double ms_mcc;                /* collisions of the candidates, field solve of the new
+                                     state and ordered absorbed lists (one kernel) */
+    double ms_post;               /* compaction+injection kernel */
     double ms_sort;               /* counting sort kernels */
     double ms_total;
     int64_t particle_steps;       /* live particles pushed, summed over steps */

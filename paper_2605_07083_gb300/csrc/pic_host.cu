@@ -18,7 +18,7 @@
 namespace pic {
 __global__ void k_push(DevState st);
 __global__ void k_deposit(DevState st);
-__global__ void k_mcc(DevState st);
+__global__ void k_mid(DevState st);
 __global__ void k_post(DevState st);
 __global__ void k_field(DevState st);
 __global__ void k_profile(DevState st);
@@ -74,7 +74,7 @@ struct pic_handle {
   // captured step loops, longest first: graph_steps steps, then every power
   // of two below it, so that any step count runs as graphs
   std::vector<std::pair<int, cudaGraphExec_t>> graphs;
-  size_t push_smem = 0, post_smem = 0, field_smem = 0;
+  size_t push_smem = 0, post_smem = 0, field_smem = 0, mid_smem = 0;
   size_t dcount_ints = 0;
   int bstart_len = 0;
   int bw_len = 0;
@@ -258,7 +258,8 @@ cudaError_t raise_smem_limits(int device) {
   cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   if (e != cudaSuccess) return e;
   const void* fns[] = {(const void*)k_push, (const void*)k_deposit, (const void*)k_field,
-                       (const void*)k_post, (const void*)k_profile, (const void*)k_phi};
+                       (const void*)k_post, (const void*)k_profile, (const void*)k_phi,
+                       (const void*)k_mid};
   for (const void* f : fns) {
     e = set_dynamic_smem_limit(f, optin);
     if (e != cudaSuccess) return e;
@@ -341,11 +342,10 @@ int set_launch_shape(pic_handle* h) {
     h->st.bstart = (int64_t*)p;
     h->bstart_len = h->G + 1;
   }
-  // compaction: staged dead list + block starts + block prefix; appends:
-  // the event keys; tail: the charge
-  const size_t species = (size_t)kDeadSmem * 4 + (size_t)(h->G + 1) * 12 + 16;
-  const size_t tail = std::max((size_t)kEvCap * 8, (size_t)h->max_nodes * 8 + 16);
-  h->post_smem = std::max(species, tail);
+  // k_mid: a diode's charge and emission histogram, or a segment's piece
+  // ranges and prefix; k_post: the staged absorbed list or the event keys
+  h->mid_smem = std::max((size_t)h->max_nodes * 20, (size_t)(h->G + 1) * 12) + 16;
+  h->post_smem = std::max((size_t)kDeadSmem * 4, (size_t)kEvCap * 8) + 16;
   // profile sampler: blocks per segment so that none bins more than
   // kHistMaxParticles particles (its 32-bit counters), else about two blocks
   // per SM in total
@@ -420,7 +420,7 @@ void launch_profile(pic_handle* h) {
 // one time step; the sort, when due, follows the step
 cudaError_t launch_step(pic_handle* h) {
   k_push<<<h->G, h->push_threads, h->push_smem, h->stream>>>(h->st);
-  k_mcc<<<h->mcc_blocks, kMccThreads, 0, h->stream>>>(h->st);
+  k_mid<<<4 * h->n_inst + h->mcc_blocks, kPostThreads, h->mid_smem, h->stream>>>(h->st);
   k_post<<<3 * h->n_inst, kPostThreads, h->post_smem, h->stream>>>(h->st);
   launch_profile(h);
   h->host_step += 1;
@@ -436,7 +436,7 @@ int build_graph(pic_handle* h, int len, cudaGraphExec_t* out) {
   if (e != cudaSuccess) return cuda_fail_at(h, e, "cudaStreamBeginCapture");
   for (int i = 0; i < len; ++i) {
     k_push<<<h->G, h->push_threads, h->push_smem, h->stream>>>(h->st);
-    k_mcc<<<h->mcc_blocks, kMccThreads, 0, h->stream>>>(h->st);
+    k_mid<<<4 * h->n_inst + h->mcc_blocks, kPostThreads, h->mid_smem, h->stream>>>(h->st);
     k_post<<<3 * h->n_inst, kPostThreads, h->post_smem, h->stream>>>(h->st);
     launch_profile(h);
     if (sort_due(h, saved + i + 1)) launch_sort(h);
@@ -813,7 +813,7 @@ int pic_profile_steps(pic_handle* h, int64_t n_steps, pic_profile* out) {
     cudaEventRecord(e[0], h->stream);
     k_push<<<h->G, h->push_threads, h->push_smem, h->stream>>>(h->st);
     cudaEventRecord(e[1], h->stream);
-    k_mcc<<<h->mcc_blocks, kMccThreads, 0, h->stream>>>(h->st);
+    k_mid<<<4 * h->n_inst + h->mcc_blocks, kPostThreads, h->mid_smem, h->stream>>>(h->st);
     cudaEventRecord(e[5], h->stream);
     k_post<<<3 * h->n_inst, kPostThreads, h->post_smem, h->stream>>>(h->st);
     launch_profile(h);

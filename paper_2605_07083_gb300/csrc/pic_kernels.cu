@@ -8,12 +8,14 @@
 //               shared-memory histogram flushed with 64-bit integer atomics.
 //               One streaming pass over z, v_z, id, staged per warp by bulk
 //               copies into shared memory.
-//   k_mcc     : the collisions of the step's candidates.
-//   k_post    : three blocks per diode, one per species: ordered absorbed-slot
-//               lists -> boundary tallies, deterministic hole-filling
-//               compaction, then the species' appends (thermionic emission;
-//               ionisation children by parent id and ion-loss replenishment)
-//               and their deposit; the last of the three solves E in FP64.
+//   k_mid     : the field of the new state, the ordered absorbed-slot lists
+//               and boundary tallies, and the collisions of the step's
+//               candidates, side by side.
+//   k_post    : three blocks per diode, one per species: deterministic
+//               hole-filling compaction, then the species' appends
+//               (thermionic emission; ionisation children by parent id and
+//               ion-loss replenishment); the last of the three closes the
+//               diode's step.
 //   k_field   : the Poisson/E solve alone (after a full deposit).
 //   k_phi     : phi and E of the current state, on request.
 //   k_profile : per-species density samples of the late-time profiles.
@@ -277,10 +279,11 @@ __device__ __forceinline__ float collide(const InstConst* __restrict__ icg, Inst
   return nvz;
 }
 
-// Apply the collisions of the step's null-collision candidates.
-__global__ void __launch_bounds__(kMccThreads) k_mcc(DevState st) {
+// The collisions of the step's null-collision candidates: thread t of a
+// stride-`stride` team takes candidates t, t + stride, ...
+__device__ void mcc_candidates(const DevState& st, unsigned t, unsigned stride) {
   const unsigned n = min(*st.cand_count, (unsigned)st.cand_cap);
-  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+  for (unsigned k = t; k < n; k += stride) {
     const unsigned long long e = st.cand_buf[k];
     const int g = (int)(e >> 32);
     const long long slot = st.seg_off[g] + (long long)(e & 0xffffffffu);
@@ -317,7 +320,7 @@ struct SegCtx {
 
 // One particle: gather, leapfrog, wall test and the null-collision candidate
 // test.  Returns bit 0 = absorbed, bit 1 = collision candidate (its
-// collision is applied afterwards by k_mcc; it changes velocities only, so
+// collision is applied afterwards by k_mid; it changes velocities only, so
 // the survivor's z is final here and is deposited by the caller).
 // Es2[j] = (E_j, E_{j+1} - E_j): one 64-bit shared load per gather
 __device__ __forceinline__ unsigned push_one(const SegCtx& c, const float2* Es2,
@@ -811,7 +814,22 @@ __device__ void update_push_weights(const DevState& st, int G, float* ws, long l
   if (threadIdx.x == 0) st.bwp[0] = 0;
 }
 
-// ------------------------------------------------------------------ k_post
+// ------------------------------------------------------------------ k_mid / k_post
+// After the push the step finishes in two kernels.
+//
+// k_mid, three kinds of blocks working side by side:
+//   * per diode, the charge and field of the new state: the survivors'
+//     charge k_push left in rho_acc plus that of the electrons emitted this
+//     step (ionisation children and replenished pairs are an electron and an
+//     ion at one position, so their charge is zero node by node), then E;
+//   * per (diode, species), the ordered list of the step's absorbed slots
+//     and the boundary tallies of Sec. 2.3 (counts, FP64 kinetic energy);
+//   * the collisions of the null-collision candidates (MCC).
+// k_post, per (diode, species): deterministic hole filling, then the
+// species' appends (thermionic electrons; ionisation children ordered by
+// parent id; replenished pairs); the last of a diode's three blocks closes
+// its step.
+
 __device__ __forceinline__ void move_particle(const DevState& st, long long off, long long src,
                                               long long dst) {
   st.z[off + dst] = st.z[off + src];
@@ -864,36 +882,30 @@ __device__ __forceinline__ void block_reduce4(long long& c0, long long& c1, doub
   __syncthreads();
 }
 
-// Linear-weight deposit of one particle per lane straight into the global
-// fixed-point charge (used for the few particles appended per step).  Lanes
-// in the cell of the warp's first active lane add their units in registers
-// first (32 x 2^24 < 2^32): the emitted electrons of a step all sit in the
-// first cells.  Called by all 32 lanes.
-__device__ __forceinline__ void deposit_global(int64_t* rho, long long sgn, float z, bool act,
-                                               float inv_dz, int Nz) {
-  int j = 0;
-  unsigned q = 0u;
-  if (act) {
-    float f;
-    cell_of(z, inv_dz, Nz, j, f);
-    q = (unsigned)frac_units(f);
+// Thermionic electrons of a step (Sec. 2.2): how many (N = floor(x) + [r <
+// frac(x)]) and electron k, a flux-weighted half-Maxwellian placed at z =
+// v_z dt.  The field blocks (charge) and the electron blocks (the particles)
+// both draw them, with the same arithmetic.
+__device__ __forceinline__ int emitted_count(const InstConst& ic, long long step) {
+  long long nem = ic.emit_floor;
+  if (ic.t_frac != 0u) {
+    const uint4 r = philox10(make_uint4(0u, (uint32_t)step, 0u, TAG_EMIT_N), ic.key0[kStreamInject],
+                             ic.key1);
+    if (r.x < ic.t_frac) nem += 1;
   }
-  const unsigned am = __ballot_sync(0xffffffffu, act);
-  if (am == 0u) return;
-  const int lead = __ffs(am) - 1;
-  const int j0 = __shfl_sync(0xffffffffu, j, lead);
-  const bool same = act && j == j0;
-  const unsigned sm = __ballot_sync(0xffffffffu, same);
-  const unsigned qs = __reduce_add_sync(0xffffffffu, same ? q : 0u);
-  unsigned long long* r = reinterpret_cast<unsigned long long*>(rho);
-  if ((int)(threadIdx.x & 31) == lead) {
-    atomicAdd(r + j0, (unsigned long long)(sgn * ((long long)__popc(sm) * kTwo24 - (long long)qs)));
-    atomicAdd(r + j0 + 1, (unsigned long long)(sgn * (long long)qs));
-  }
-  if (act && !same) {
-    atomicAdd(r + j, (unsigned long long)(sgn * ((long long)kTwo24 - (long long)q)));
-    atomicAdd(r + j + 1, (unsigned long long)(sgn * (long long)q));
-  }
+  return (int)nem;
+}
+
+__device__ __forceinline__ void emitted_electron(const InstConst& ic, int k, long long step,
+                                                 float& z, float& vx, float& vy, float& vz) {
+  const uint4 r = philox10(make_uint4((uint32_t)k, (uint32_t)step, 0u, TAG_EMIT),
+                           ic.key0[kStreamInject], ic.key1);
+  float n0, n1;
+  box_muller(r.x, r.y, n0, n1);
+  vz = ic.sig_w * sqrtf(-2.0f * logf(u01f(r.z)));
+  z = vz * ic.dt_f;
+  vx = ic.sig_w * n0;
+  vy = ic.sig_w * n1;
 }
 
 // Ionisation events of the step ordered by parent id: keys (parent << 32 | k)
@@ -925,38 +937,174 @@ __device__ void sort_events(const Event* evb, int E, unsigned long long* evk) {
   }
 }
 
-// Three blocks per diode, one per species.  Each compacts its species
-// (ordered absorbed list, boundary tallies, deterministic hole filling) and
-// appends the species' new particles of the step -- thermionic electrons
-// (species 0), ionisation children and replenished pairs (species 1 and 2)
-// -- depositing them into the fixed-point charge.  The particle ids of all
-// appends follow from counts every block can compute (events, emission count,
-// ions absorbed), so the blocks need nothing from one another.  The last of
-// the three to finish (an arrival counter; nothing waits) solves the field
-// and closes the diode's step.
-__global__ void __launch_bounds__(kPostThreads, 1) k_post(DevState st) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ long long wsl[64];
-  __shared__ double wsd2[64];
-  __shared__ long long ws64[32];
-  __shared__ int ws32[32];
+// Field of the new state of one diode (k_mid).
+__device__ void mid_field(const DevState& st, int inst, unsigned char* smem, long long* ws64) {
   __shared__ InstConst ic;
-  __shared__ int sE, sNemit, sLast;
-  __shared__ long long sCnt[3][2];
-  __shared__ double sKe[3][2];
-  __shared__ int sN[3], sD[3];
-
-  const int inst = blockIdx.x / 3, sp = blockIdx.x - 3 * inst;
+  __shared__ int sNemit;
   const int tid = threadIdx.x, nt = blockDim.x;
   {
     const int* src = reinterpret_cast<const int*>(st.ic + inst);
     int* dst = reinterpret_cast<int*>(&ic);
     for (int w = tid; w < (int)(sizeof(InstConst) / 4); w += nt) dst[w] = src[w];
   }
-  __syncthreads();                 // ic is read by every thread below
+  __syncthreads();
+  const long long step = st.dyn[inst].step;
+  const int nn = ic.Nz + 1, off = ic.node_off;
+  long long* rho_s = reinterpret_cast<long long*>(smem);            // [nn]
+  Hist h;                                                           // emitted electrons
+  h.h3 = reinterpret_cast<unsigned*>(rho_s + nn);
+  int64_t* acc = st.rho_acc + off;
+  for (int j = tid; j < nn; j += nt) rho_s[j] = acc[j];
+  hist_zero(h, ic.Nz);
+  if (tid == 0) sNemit = emitted_count(ic, step);
+  __syncthreads();
+  const int Nemit = sNemit;
+  for (int base = 0; base < Nemit; base += nt) {
+    const int k = base + tid;
+    float zz[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    unsigned am = 0u;
+    if (k < Nemit) {
+      float vx, vy, vz;
+      emitted_electron(ic, k, step, zz[0], vx, vy, vz);
+      am = 1u;
+    }
+    deposit_warp(h, zz, am, ic.inv_dz_f, ic.Nz, true);
+  }
+  __syncthreads();
+  for (int j = tid; j < nn; j += nt) {
+    const long long v = rho_s[j] - hist_node(h, j, ic.Nz);
+    rho_s[j] = v;
+    st.rho[off + j] = v;
+    acc[j] = 0;
+  }
+  __syncthreads();
+  const bool sample = profile_due(st.prof_period, ic.window_start, step);
+  field_solve(ic, rho_s, st.E + off, sample ? st.phi + off : nullptr, ws64);
+  if (sample) {
+    double* pa = st.phi_sum + off;
+    const double* ph = st.phi + off;
+    for (int j = tid; j < nn; j += nt) pa[j] += ph[j];
+    if (tid == 0) st.prof_n[inst] += 1;
+  }
+}
+
+// Ordered absorbed-slot list of one segment and its boundary tallies (k_mid):
+// the push pieces' lists, concatenated in slot order, into dead_buf + off;
+// count, live count before the step and tallies into the diode's hand-off
+// record.
+__device__ void mid_absorbed(const DevState& st, int g, unsigned char* smem, int* ws32,
+                             long long* wsl, double* wsd) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int inst = g / 3, sp = g - 3 * inst;
+  const int Geff = (int)st.part[st.n_seg + 1];
+  const long long off = st.seg_off[g];
+  const int N = st.seg_count[g];
+  const long long qg = (N + 3) >> 2;
+  const long long Sg = st.part[g];
+  long long* blo = reinterpret_cast<long long*>(smem);               // [Geff + 1]
+  int* bpre = reinterpret_cast<int*>(blo + Geff + 1);                // [Geff + 1]
+  for (int b = tid; b <= Geff; b += nt) blo[b] = st.bstart[b];
+  __syncthreads();
+  int carry = 0;
+  for (int base = 0; base < Geff; base += nt) {
+    const int b = base + tid;
+    int c = 0;
+    if (b < Geff) {
+      const long long lb = blo[b], hb = blo[b + 1];
+      if (qg > 0 && lb < hb && lb < Sg + qg && hb > Sg) c = st.dcount[(long long)g * st.G + b];
+    }
+    int tot;
+    const int ex = block_exclusive_scan<int>(c, &tot, ws32);
+    if (b < Geff) bpre[b] = carry + ex;
+    carry += tot;
+  }
+  if (tid == 0) bpre[Geff] = carry;
+  __syncthreads();
+  const int D = carry;
+  uint32_t* dd = st.dead_buf + off;
+  const InstConst& ic = st.ic[inst];
+  const double mw = 0.5 * ic.m_d[sp] * ic.weight;
+  long long cnt0 = 0, cnt1 = 0;
+  double ke0 = 0.0, ke1 = 0.0;
+  for (int k = tid; k < D; k += nt) {
+    int blo_i = 0, bhi_i = Geff;
+    while (bhi_i - blo_i > 1) {
+      const int mid = (blo_i + bhi_i) >> 1;
+      if (bpre[mid] <= k) blo_i = mid; else bhi_i = mid;
+    }
+    const long long lb = blo[blo_i];
+    const long long q0b = (lb > Sg ? lb : Sg) - Sg;
+    const uint32_t idx = st.dead_dense[off + 4 * q0b + (k - bpre[blo_i])];
+    dd[k] = idx;
+    const float z = st.z[off + idx];
+    const double vx = st.vx[off + idx], vy = st.vy[off + idx], vz = st.vz[off + idx];
+    const double ke = mw * (vx * vx + vy * vy + vz * vz);
+    if (z < 0.0f) { cnt0 += 1; ke0 += ke; } else { cnt1 += 1; ke1 += ke; }
+  }
+  block_reduce4(cnt0, cnt1, ke0, ke1, wsl, wsd);
+  if (tid == 0) {
+    PostScratch* ps = st.post + inst;
+    ps->D[sp] = D;
+    ps->N[sp] = N;
+    ps->cnt[sp][0] = cnt0;
+    ps->cnt[sp][1] = cnt1;
+    ps->ke[sp][0] = ke0;
+    ps->ke[sp][1] = ke1;
+  }
+}
+
+// Blocks [0, n_inst): field of diode b.  [n_inst, 4 n_inst): absorbed list
+// and tallies of segment b - n_inst.  The rest: the candidates' collisions
+// (the first of them also re-weights the push blocks for the next step).
+__global__ void __launch_bounds__(kPostThreads, 2) k_mid(DevState st) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long wsl[64];
+  __shared__ double wsd[64];
+  __shared__ long long ws64[32];
+  __shared__ int ws32[32];
+  const int b = blockIdx.x, ni = st.n_inst;
+  if (b < ni) {
+    mid_field(st, b, smem, ws64);
+  } else if (b < 4 * ni) {
+    mid_absorbed(st, b - ni, smem, ws32, wsl, wsd);
+  } else {
+    const int m = b - 4 * ni;
+    mcc_candidates(st, (unsigned)m * blockDim.x + threadIdx.x,
+                   (unsigned)(gridDim.x - 4 * ni) * blockDim.x);
+    if (m == 0) {
+      __syncthreads();
+      update_push_weights(st, (int)st.part[st.n_seg + 1], reinterpret_cast<float*>(wsd), ws64);
+    }
+  }
+}
+
+// Three blocks per diode, one per species: deterministic hole filling of the
+// species' absorbed slots (the ordered list k_mid left in dead_buf), then
+// its appends -- thermionic electrons (species 0), ionisation children
+// sorted by parent id and replenished pairs (species 1 and 2) -- with ids and
+// slots every block derives from counts it can read (events, emission
+// count, ions absorbed).  The last of the three to finish (an arrival
+// counter; nothing waits) closes the diode's step.
+__global__ void __launch_bounds__(kPostThreads, 1) k_post(DevState st) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int ws32[32];
+  __shared__ InstConst ic;
+  __shared__ int sE, sNemit, sLast, sD, sN, sDi;
+
+  const int inst = blockIdx.x / 3, sp = blockIdx.x - 3 * inst;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (blockIdx.x == 0 && tid == 0) {
+    // k_mid has consumed the candidates
+    if (*st.cand_count > (unsigned)st.cand_cap) atomicOr(&st.dyn[0].err, ERR_CAPACITY);
+    *st.cand_count = 0u;
+  }
+  {
+    const int* src = reinterpret_cast<const int*>(st.ic + inst);
+    int* dst = reinterpret_cast<int*>(&ic);
+    for (int w = tid; w < (int)(sizeof(InstConst) / 4); w += nt) dst[w] = src[w];
+  }
   InstDyn* dyn = st.dyn + inst;
   PostScratch* ps = st.post + inst;
-  const int Geff = (int)st.part[st.n_seg + 1];
   const long long step = dyn->step;
   const uint32_t base_id = dyn->next_id;
   if (tid == 0) {
@@ -966,74 +1114,28 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post(DevState st) {
       e = kEvCap;
     }
     sE = e;
-    long long nem = ic.emit_floor;
-    if (ic.t_frac != 0u) {
-      const uint4 r = philox10(make_uint4(0u, (uint32_t)step, 0u, TAG_EMIT_N), ic.key0[kStreamInject], ic.key1);
-      if (r.x < ic.t_frac) nem += 1;
-    }
-    sNemit = (int)nem;
+    sD = ps->D[sp];
+    sN = ps->N[sp];
+    sDi = ps->D[2];
   }
+  __syncthreads();                 // ic and the counts are read by every thread below
+  if (tid == 0) sNemit = emitted_count(ic, step);
 
-  // ---- compaction of this species
+  // ---- hole filling: the dead slots below the new count take the live
+  // particles above it, in order
   const int g = inst * 3 + sp;
   const long long off = st.seg_off[g];
-  const int N = st.seg_count[g];
   const int cap = st.seg_cap[g];
-  int D, Nn, P;
-  long long cnt0 = 0, cnt1 = 0;
-  double ke0 = 0.0, ke1 = 0.0;
+  const int D = sD, N = sN;
+  const int Nn = N - D;
   {
-    uint32_t* dd_s = reinterpret_cast<uint32_t*>(smem);                 // kDeadSmem slots
-    long long* blo = reinterpret_cast<long long*>(dd_s + kDeadSmem);    // [Geff + 1]
-    int* bpre = reinterpret_cast<int*>(blo + Geff + 1);                 // [Geff + 1]
-    const long long qg = (N + 3) >> 2;
-    const long long Sg = st.part[g];
-    // the ions' quad range, for the replenishment count of the electron block
-    const int gi = inst * 3 + 2;
-    const long long Si = st.part[gi], qi = st.part[gi + 1] - Si;
-    const bool need_ions = ic.replenish && sp == 1;
-    for (int b = tid; b <= Geff; b += nt) blo[b] = st.bstart[b];
-    __syncthreads();
-    int carry = 0, ions = 0;
-    for (int base = 0; base < Geff; base += nt) {
-      const int b = base + tid;
-      int c = 0;
-      if (b < Geff) {
-        const long long lb = blo[b], hb = blo[b + 1];
-        if (qg > 0 && lb < hb && lb < Sg + qg && hb > Sg) c = st.dcount[(long long)g * st.G + b];
-        if (need_ions && qi > 0 && lb < hb && lb < Si + qi && hb > Si)
-          ions += st.dcount[(long long)gi * st.G + b];
-      }
-      int tot;
-      const int ex = block_exclusive_scan<int>(c, &tot, ws32);
-      if (b < Geff) bpre[b] = carry + ex;
-      carry += tot;
+    uint32_t* dd = st.dead_buf + off;
+    if (D <= kDeadSmem) {
+      uint32_t* dd_s = reinterpret_cast<uint32_t*>(smem);
+      for (int k = tid; k < D; k += nt) dd_s[k] = dd[k];
+      dd = dd_s;
     }
-    if (tid == 0) bpre[Geff] = carry;
-    if (need_ions) ions = block_sum<int>(ions, ws32);
     __syncthreads();
-    D = carry;
-    uint32_t* dd = (D <= kDeadSmem) ? dd_s : st.dead_buf + off;
-    const double mw = 0.5 * ic.m_d[sp] * ic.weight;
-    for (int k = tid; k < D; k += nt) {
-      int blo_i = 0, bhi_i = Geff;
-      while (bhi_i - blo_i > 1) {
-        const int mid = (blo_i + bhi_i) >> 1;
-        if (bpre[mid] <= k) blo_i = mid; else bhi_i = mid;
-      }
-      const long long lb = blo[blo_i];
-      const long long q0b = (lb > Sg ? lb : Sg) - Sg;
-      const uint32_t idx = st.dead_dense[off + 4 * q0b + (k - bpre[blo_i])];
-      dd[k] = idx;
-      const float z = st.z[off + idx];
-      const double vx = st.vx[off + idx], vy = st.vy[off + idx], vz = st.vz[off + idx];
-      const double ke = mw * (vx * vx + vy * vy + vz * vz);
-      if (z < 0.0f) { cnt0 += 1; ke0 += ke; } else { cnt1 += 1; ke1 += ke; }
-    }
-    block_reduce4(cnt0, cnt1, ke0, ke1, wsl, wsd2);   // also orders dd writes
-    // hole filling: the dead slots below the new count take the live
-    // particles above it, in order
-    Nn = N - D;
     int lo = 0, hi = D;
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
@@ -1058,182 +1160,103 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post(DevState st) {
       if (live) move_particle(st, off, t, dd[r]);
       run += tot;
     }
-    P = !ic.replenish ? 0 : (sp == 2 ? D : (sp == 1 ? ions : 0));
     __syncthreads();                 // shared memory is reused below
   }
 
-  // ---- appends of this species and their charge
+  // ---- appends of this species (their charge is in the field already)
   const int E = sE, Nemit = sNemit;
+  const int P = !ic.replenish ? 0 : (sp == 0 ? 0 : sDi);
   const uint32_t id_emit = base_id + 2u * (uint32_t)E;
   const uint32_t id_repl = id_emit + (uint32_t)Nemit;
-  int64_t* rho = st.rho_acc + ic.node_off;
   bool overflow = false;
   int newN = Nn;
   if (sp == 0) {
-    // thermionic electrons (Sec. 2.2): flux-weighted half-Maxwellian, z = v_z dt
-    for (int base = 0; base < Nemit; base += nt) {
-      const int k = base + tid;
-      bool act = false;
-      float z = 0.0f;
-      if (k < Nemit) {
-        const uint4 r = philox10(make_uint4((uint32_t)k, (uint32_t)step, 0u, TAG_EMIT),
-                                 ic.key0[kStreamInject], ic.key1);
-        float n0, n1;
-        box_muller(r.x, r.y, n0, n1);
-        const float vz = ic.sig_w * sqrtf(-2.0f * logf(u01f(r.z)));
-        z = vz * ic.dt_f;
-        const long long sl = (long long)Nn + k;
-        if (sl < cap) {
-          put_particle(st, off, sl, z, ic.sig_w * n0, ic.sig_w * n1, vz, id_emit + (uint32_t)k);
-          act = true;
-        } else {
-          overflow = true;
-        }
-      }
-      deposit_global(rho, -1LL, z, act, ic.inv_dz_f, ic.Nz);
+    for (int k = tid; k < Nemit; k += nt) {
+      float z, vx, vy, vz;
+      emitted_electron(ic, k, step, z, vx, vy, vz);
+      const long long sl = (long long)Nn + k;
+      if (sl < cap) put_particle(st, off, sl, z, vx, vy, vz, id_emit + (uint32_t)k);
+      else overflow = true;
     }
     newN = min(Nn + Nemit, cap);
   } else {
-    const long long sgn = (sp == 2) ? 1LL : -1LL;
     const uint32_t idb = (sp == 2) ? 1u : 0u;
     // ionisation children (Sec. 2.2 reading): the electron as a plasma
     // electron, the ion at the neutral's velocity, ordered by parent id
     unsigned long long* evk = reinterpret_cast<unsigned long long*>(smem);
     const Event* evb = st.ev_buf + (long long)inst * kEvCap;
     sort_events(evb, E, evk);
-    for (int base = 0; base < E; base += nt) {
-      const int k = base + tid;
-      bool act = false;
-      float z = 0.0f;
-      if (k < E) {
-        const Event ev = evb[(int)(evk[k] & 0xffffffffu)];
-        z = ev.z;
-        const long long sl = (long long)Nn + k;
-        if (sl < cap) {
-          const bool ion = sp == 2;
-          put_particle(st, off, sl, z, ion ? ev.vi[0] : ev.ve[0], ion ? ev.vi[1] : ev.ve[1],
-                       ion ? ev.vi[2] : ev.ve[2], base_id + 2u * k + idb);
-          act = true;
-        } else {
-          overflow = true;
-        }
+    for (int k = tid; k < E; k += nt) {
+      const Event ev = evb[(int)(evk[k] & 0xffffffffu)];
+      const long long sl = (long long)Nn + k;
+      if (sl < cap) {
+        const bool ion = sp == 2;
+        put_particle(st, off, sl, ev.z, ion ? ev.vi[0] : ev.ve[0], ion ? ev.vi[1] : ev.ve[1],
+                     ion ? ev.vi[2] : ev.ve[2], base_id + 2u * k + idb);
+      } else {
+        overflow = true;
       }
-      deposit_global(rho, sgn, z, act, ic.inv_dz_f, ic.Nz);
     }
     // replenishment (Sec. 2.1): one e-ion pair at a common uniform position
     // per ion absorbed; both blocks draw the pair's numbers
     const float sig = (sp == 2) ? ic.sig_i0 : ic.sig_e0;
-    for (int base = 0; base < P; base += nt) {
-      const int k = base + tid;
-      bool act = false;
-      float z = 0.0f;
-      if (k < P) {
-        const uint4 A = philox10(make_uint4((uint32_t)k, (uint32_t)step, 0u, TAG_REPL), ic.key0[kStreamInject], ic.key1);
-        const uint4 B = philox10(make_uint4((uint32_t)k, (uint32_t)step, 1u, TAG_REPL), ic.key0[kStreamInject], ic.key1);
-        float gg[6];
-        box_muller(A.x, A.y, gg[0], gg[1]);
-        box_muller(A.z, A.w, gg[2], gg[3]);
-        box_muller(B.x, B.y, gg[4], gg[5]);
-        z = u01f(B.z) * ic.L_f;
-        const long long sl = (long long)Nn + E + k;
-        if (sl < cap) {
-          const bool ion = sp == 2;
-          put_particle(st, off, sl, z, sig * (ion ? gg[3] : gg[0]), sig * (ion ? gg[4] : gg[1]),
-                       sig * (ion ? gg[5] : gg[2]), id_repl + 2u * k + idb);
-          act = true;
-        } else {
-          overflow = true;
-        }
+    for (int k = tid; k < P; k += nt) {
+      const uint4 A = philox10(make_uint4((uint32_t)k, (uint32_t)step, 0u, TAG_REPL), ic.key0[kStreamInject], ic.key1);
+      const uint4 B = philox10(make_uint4((uint32_t)k, (uint32_t)step, 1u, TAG_REPL), ic.key0[kStreamInject], ic.key1);
+      float gg[6];
+      box_muller(A.x, A.y, gg[0], gg[1]);
+      box_muller(A.z, A.w, gg[2], gg[3]);
+      box_muller(B.x, B.y, gg[4], gg[5]);
+      const float z = u01f(B.z) * ic.L_f;
+      const long long sl = (long long)Nn + E + k;
+      if (sl < cap) {
+        const bool ion = sp == 2;
+        put_particle(st, off, sl, z, sig * (ion ? gg[3] : gg[0]), sig * (ion ? gg[4] : gg[1]),
+                     sig * (ion ? gg[5] : gg[2]), id_repl + 2u * k + idb);
+      } else {
+        overflow = true;
       }
-      deposit_global(rho, sgn, z, act, ic.inv_dz_f, ic.Nz);
     }
     newN = min(Nn + E + P, cap);
   }
   if (__syncthreads_or(overflow) && tid == 0) atomicOr(&dyn->err, ERR_CAPACITY);
-  // the plasma-electron block of diode 0 (usually the lightest) re-weights
-  // the push blocks for the next step
-  if ((int)blockIdx.x == 1) update_push_weights(st, Geff, reinterpret_cast<float*>(wsd2), ws64);
 
-  // every thread's moves, appends and charge are complete and visible before
-  // the arrival
+  // every thread's moves and appends are complete and visible before the
+  // arrival
   __threadfence();
   __syncthreads();
   if (tid == 0) {
     st.seg_count[g] = newN;
-    ps->D[sp] = D;
-    ps->N[sp] = N;
-    ps->Nn[sp] = Nn;
-    ps->cnt[sp][0] = cnt0;
-    ps->cnt[sp][1] = cnt1;
-    ps->ke[sp][0] = ke0;
-    ps->ke[sp][1] = ke1;
     __threadfence();
     sLast = (atomicAdd(&ps->arrive, 1u) == 2u);
   }
   __syncthreads();
-  if (!sLast) return;
+  if (!sLast || tid != 0) return;
 
-  // ---- tail: the last species block of this diode
+  // ---- the last species block of this diode: window tallies, ids, step
   __threadfence();
-  if (tid == 0) {
-    const volatile PostScratch* vp = ps;
-    for (int k = 0; k < 3; ++k) {
-      sD[k] = vp->D[k];
-      sN[k] = vp->N[k];
-      sCnt[k][0] = vp->cnt[k][0];
-      sCnt[k][1] = vp->cnt[k][1];
-      sKe[k][0] = vp->ke[k][0];
-      sKe[k][1] = vp->ke[k][1];
-    }
-    ps->arrive = 0u;
-    if (inst == 0) {
-      if (*st.cand_count > (unsigned)st.cand_cap) atomicOr(&dyn->err, ERR_CAPACITY);
-      *st.cand_count = 0u;
-    }
+  const volatile PostScratch* vp = ps;
+  ps->arrive = 0u;
+  const int Pt = ic.replenish ? vp->D[2] : 0;
+  dyn->next_id = id_repl + 2u * (uint32_t)Pt;
+  // ids key the random streams: a diode that has handed out all 2^32 of
+  // them would reuse one, so that is reported as running out of capacity
+  if ((unsigned long long)base_id + 2ull * (unsigned)E + (unsigned)Nemit + 2ull * (unsigned)Pt >
+      0xFFFFFFFFull)
+    atomicOr(&dyn->err, ERR_CAPACITY);
+  if (step >= ic.window_start) {
+    dyn->win_steps += 1;
+    for (int k = 0; k < 3; ++k)
+      for (int w = 0; w < 2; ++w) {
+        dyn->count[k][w] += vp->cnt[k][w];
+        dyn->ke[k][w] += vp->ke[k][w];
+      }
+    dyn->emitted += Nemit;
+    dyn->replenished += Pt;
   }
-  __syncthreads();
-  // charge of the new state and its field
-  long long* rho_s = reinterpret_cast<long long*>(smem);
-  const int nn = ic.Nz + 1;
-  for (int j = tid; j < nn; j += nt) {
-    const long long v = ((volatile long long*)rho)[j];
-    rho_s[j] = v;
-    st.rho[ic.node_off + j] = v;
-    rho[j] = 0;
-  }
-  __syncthreads();
-  const bool sample = profile_due(st.prof_period, ic.window_start, step);
-  field_solve(ic, rho_s, st.E + ic.node_off, sample ? st.phi + ic.node_off : nullptr, ws64);
-  if (sample) {
-    double* pa = st.phi_sum + ic.node_off;
-    const double* ph = st.phi + ic.node_off;
-    for (int j = tid; j < nn; j += nt) pa[j] += ph[j];
-    if (tid == 0) st.prof_n[inst] += 1;
-  }
-
-  // window tallies, ids, step
-  if (tid == 0) {
-    const int Pt = ic.replenish ? sD[2] : 0;
-    dyn->next_id = id_repl + 2u * (uint32_t)Pt;
-    // ids key the random streams: a diode that has handed out all 2^32 of
-    // them would reuse one, so that is reported as running out of capacity
-    if ((unsigned long long)base_id + 2ull * (unsigned)E + (unsigned)Nemit + 2ull * (unsigned)Pt >
-        0xFFFFFFFFull)
-      atomicOr(&dyn->err, ERR_CAPACITY);
-    if (step >= ic.window_start) {
-      dyn->win_steps += 1;
-      for (int k = 0; k < 3; ++k)
-        for (int w = 0; w < 2; ++w) {
-          dyn->count[k][w] += sCnt[k][w];
-          dyn->ke[k][w] += sKe[k][w];
-        }
-      dyn->emitted += Nemit;
-      dyn->replenished += Pt;
-    }
-    dyn->pushed += (long long)sN[0] + sN[1] + sN[2];
-    dyn->ev_count = 0;
-    dyn->step = step + 1;
-  }
+  dyn->pushed += (long long)vp->N[0] + vp->N[1] + vp->N[2];
+  dyn->ev_count = 0;
+  dyn->step = step + 1;
 }
 
 // ------------------------------------------------------------------ profiles
