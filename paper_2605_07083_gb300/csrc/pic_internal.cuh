@@ -72,7 +72,7 @@ struct InstDyn {
   uint32_t next_id;
   int32_t ev_count;
   int32_t err;
-  int32_t pad;
+  int32_t emit_dep;          // 1: a push block binned this step's emitted electrons
   int64_t win_steps;
   int64_t count[3][2];
   double ke[3][2];
@@ -386,6 +386,49 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* total, T* ws) {
   *total = ws[nw - 1];
   __syncthreads();
   return base + x - v;
+}
+
+// Exclusive scan of the first of two 64-bit values per thread and the block
+// total of the second, in one pass.  ws: shared scratch of >= 32 elements.
+// Must be called by all threads.
+__device__ __forceinline__ void block_exclusive_scan_pair(long long x, long long y, long long* ex,
+                                                          long long* ytot, long long* ws) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  long long a = x, b = y;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long pa = __shfl_up_sync(0xffffffffu, a, o);
+    const long long pb = __shfl_up_sync(0xffffffffu, b, o);
+    if (lane >= o) {
+      a += pa;
+      b += pb;
+    }
+  }
+  __shared__ long long wsb[32];
+  if (lane == 31) {
+    ws[wid] = a;
+    wsb[wid] = b;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    long long wa = (lane < nw) ? ws[lane] : 0LL, wb = (lane < nw) ? wsb[lane] : 0LL;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long pa = __shfl_up_sync(0xffffffffu, wa, o);
+      const long long pb = __shfl_up_sync(0xffffffffu, wb, o);
+      if (lane >= o) {
+        wa += pa;
+        wb += pb;
+      }
+    }
+    ws[lane] = wa;
+    wsb[lane] = wb;
+  }
+  __syncthreads();
+  *ex = ((wid > 0) ? ws[wid - 1] : 0LL) + a - x;
+  *ytot = wsb[nw - 1];
+  __syncthreads();
 }
 
 template <typename T>

@@ -310,6 +310,32 @@ __device__ void mcc_candidates(const DevState& st, unsigned t, unsigned stride) 
   }
 }
 
+// Thermionic electrons of a step (Sec. 2.2): how many (N = floor(x) + [r <
+// frac(x)]) and electron k, a flux-weighted half-Maxwellian placed at z =
+// v_z dt.  The field blocks (charge) and the electron blocks (the particles)
+// both draw them, with the same arithmetic.
+__device__ __forceinline__ int emitted_count(const InstConst& ic, long long step) {
+  long long nem = ic.emit_floor;
+  if (ic.t_frac != 0u) {
+    const uint4 r = philox10(make_uint4(0u, (uint32_t)step, 0u, TAG_EMIT_N), ic.key0[kStreamInject],
+                             ic.key1);
+    if (r.x < ic.t_frac) nem += 1;
+  }
+  return (int)nem;
+}
+
+__device__ __forceinline__ void emitted_electron(const InstConst& ic, int k, long long step,
+                                                 float& z, float& vx, float& vy, float& vz) {
+  const uint4 r = philox10(make_uint4((uint32_t)k, (uint32_t)step, 0u, TAG_EMIT),
+                           ic.key0[kStreamInject], ic.key1);
+  float n0, n1;
+  box_muller(r.x, r.y, n0, n1);
+  vz = ic.sig_w * sqrtf(-2.0f * logf(u01f(r.z)));
+  z = vz * ic.dt_f;
+  vx = ic.sig_w * n0;
+  vy = ic.sig_w * n1;
+}
+
 // ------------------------------------------------------------------ k_push
 struct SegCtx {
   float inv_dz, Lf, dt, qmdt;
@@ -496,6 +522,25 @@ __device__ __forceinline__ void push_body(const DevState& st) {
       const int b1 = (q1 - a > kSubQuads) ? a + kSubQuads : q1;
       hist_zero(hist, icS.Nz);
       __syncthreads();
+      if (!kDepositOnly && sp < 2 && a == 0 && s0 == segS[3 * inst]) {
+        // this block holds the diode's first particle, an electron: it also
+        // bins the charge of the electrons the step emits (Sec. 2.2), so the
+        // field of the new state needs nothing more than the push's charge
+        const long long step = st.dyn[inst].step;
+        const int Nemit = emitted_count(icS, step);
+        for (int base = 0; base < Nemit; base += blockDim.x) {
+          const int k = base + threadIdx.x;
+          float ze[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+          unsigned am = 0u;
+          if (k < Nemit) {
+            float vx, vy, vz;
+            emitted_electron(icS, k, step, ze[0], vx, vy, vz);
+            am = 1u;
+          }
+          deposit_warp(hist, ze, am, icS.inv_dz_f, icS.Nz, true);
+        }
+        if (threadIdx.x == 0) st.dyn[inst].emit_dep = 1;
+      }
       const int wq0 = (int)warp_start(a, b1, warp, W), wq1 = (int)warp_start(a, b1, warp + 1, W);
       const long long off = st.seg_off[g];
       const int N = st.seg_count[g];
@@ -691,54 +736,56 @@ __device__ void field_solve(const InstConst& ic, long long* rho_s, float* E, dou
   const int c = (Nz + nt - 1) / nt;            // <= 8 for Nz <= 4096, nt = 512
   const int j0 = threadIdx.x * c;
   long long a[8];
-  long long loc = 0;
+  long long loc = 0, wl = 0;                   // sum rho_k; sum rho_k (Nz - k)
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     if (u < c) {
       const int j = j0 + u;
       const long long v = (j >= 1 && j < Nz) ? rho_s[j] : 0LL;
       loc += v;
+      wl += v * (long long)(Nz - j);
       a[u] = loc;
     }
   }
-  long long tot;
-  const long long ex = block_exclusive_scan<long long>(loc, &tot, ws);
-  long long hx[8];
-  long long lsum = 0;
-#pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    if (u < c) {
-      a[u] += ex;
-      if (j0 + u < Nz) {
-        hx[u] = lsum;
-        lsum += a[u];
-      }
-    }
-  }
-  long long Htot;
-  long long hex = 0;
-  if (phi) hex = block_exclusive_scan<long long>(lsum, &Htot, ws);
-  else Htot = block_sum<long long>(lsum, ws);
-#pragma unroll
-  for (int u = 0; u < 8; ++u)
-    if (u < c && j0 + u < Nz) rho_s[j0 + u] = a[u];
-  __syncthreads();
+  // one scan of the pair: the exclusive prefix of loc is G at the node
+  // before this thread's first; the total of wl is sum_{j < Nz} G_j
+  long long ex, Htot;
+  block_exclusive_scan_pair(loc, wl, &ex, &Htot, ws);
   // E_j = -(d_j + d_{j-1}) / (2 dz) = A + B (G_j + G_{j-1}),  A = -d0/dz, B = kappa/(2 dz)
   const double kap = ic.kappa;
   const double d0 = (ic.V + kap * (double)Htot) * ic.inv_nz;
   const double A = -d0 * ic.inv_dz, B = 0.5 * kap * ic.inv_dz;
+  long long gprev = ex;                        // G_{j0 - 1}
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     const int j = j0 + u;
     if (u < c && j < Nz) {
-      const long long gsum = (j == 0) ? 0LL : a[u] + rho_s[j - 1];
+      const long long gj = ex + a[u];
+      const long long gsum = (j == 0) ? 0LL : gj + gprev;
       E[j] = (float)fma(B, (double)gsum, A);
-      if (phi) phi[j] = fma((double)j, d0, -kap * (double)(hex + hx[u]));
+      gprev = gj;
+      a[u] = gj;
     }
   }
-  if (threadIdx.x == 0) {
-    E[Nz] = (float)fma(2.0 * B, (double)rho_s[Nz - 1], A);
-    if (phi) phi[Nz] = ic.V;
+  if (j0 < Nz && j0 + c >= Nz) E[Nz] = (float)fma(2.0 * B, (double)gprev, A);   // G_{Nz-1}
+  if (phi) {
+    // phi_j = j d0 - kappa sum_{k<j} G_k: a second scan, for sampled or
+    // requested potentials only
+    long long lsum = 0, hx[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (u < c && j0 + u < Nz) {
+        hx[u] = lsum;
+        lsum += a[u];
+      }
+    long long tot;
+    const long long hex = block_exclusive_scan<long long>(lsum, &tot, ws);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int j = j0 + u;
+      if (u < c && j < Nz) phi[j] = fma((double)j, d0, -kap * (double)(hex + hx[u]));
+    }
+    if (threadIdx.x == 0) phi[Nz] = ic.V;
   }
   __syncthreads();
 }
@@ -882,32 +929,6 @@ __device__ __forceinline__ void block_reduce4(long long& c0, long long& c1, doub
   __syncthreads();
 }
 
-// Thermionic electrons of a step (Sec. 2.2): how many (N = floor(x) + [r <
-// frac(x)]) and electron k, a flux-weighted half-Maxwellian placed at z =
-// v_z dt.  The field blocks (charge) and the electron blocks (the particles)
-// both draw them, with the same arithmetic.
-__device__ __forceinline__ int emitted_count(const InstConst& ic, long long step) {
-  long long nem = ic.emit_floor;
-  if (ic.t_frac != 0u) {
-    const uint4 r = philox10(make_uint4(0u, (uint32_t)step, 0u, TAG_EMIT_N), ic.key0[kStreamInject],
-                             ic.key1);
-    if (r.x < ic.t_frac) nem += 1;
-  }
-  return (int)nem;
-}
-
-__device__ __forceinline__ void emitted_electron(const InstConst& ic, int k, long long step,
-                                                 float& z, float& vx, float& vy, float& vz) {
-  const uint4 r = philox10(make_uint4((uint32_t)k, (uint32_t)step, 0u, TAG_EMIT),
-                           ic.key0[kStreamInject], ic.key1);
-  float n0, n1;
-  box_muller(r.x, r.y, n0, n1);
-  vz = ic.sig_w * sqrtf(-2.0f * logf(u01f(r.z)));
-  z = vz * ic.dt_f;
-  vx = ic.sig_w * n0;
-  vy = ic.sig_w * n1;
-}
-
 // Ionisation events of the step ordered by parent id: keys (parent << 32 | k)
 // in evk[0, P2), bitonic sort in shared memory.
 __device__ void sort_events(const Event* evb, int E, unsigned long long* evk) {
@@ -951,33 +972,40 @@ __device__ void mid_field(const DevState& st, int inst, unsigned char* smem, lon
   const long long step = st.dyn[inst].step;
   const int nn = ic.Nz + 1, off = ic.node_off;
   long long* rho_s = reinterpret_cast<long long*>(smem);            // [nn]
-  Hist h;                                                           // emitted electrons
-  h.h3 = reinterpret_cast<unsigned*>(rho_s + nn);
   int64_t* acc = st.rho_acc + off;
-  for (int j = tid; j < nn; j += nt) rho_s[j] = acc[j];
-  hist_zero(h, ic.Nz);
-  if (tid == 0) sNemit = emitted_count(ic, step);
-  __syncthreads();
-  const int Nemit = sNemit;
-  for (int base = 0; base < Nemit; base += nt) {
-    const int k = base + tid;
-    float zz[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    unsigned am = 0u;
-    if (k < Nemit) {
-      float vx, vy, vz;
-      emitted_electron(ic, k, step, zz[0], vx, vy, vz);
-      am = 1u;
-    }
-    deposit_warp(h, zz, am, ic.inv_dz_f, ic.Nz, true);
-  }
-  __syncthreads();
   for (int j = tid; j < nn; j += nt) {
-    const long long v = rho_s[j] - hist_node(h, j, ic.Nz);
-    rho_s[j] = v;
-    st.rho[off + j] = v;
+    rho_s[j] = acc[j];
     acc[j] = 0;
   }
+  if (tid == 0) {
+    sNemit = st.dyn[inst].emit_dep ? 0 : emitted_count(ic, step);
+    st.dyn[inst].emit_dep = 0;
+  }
   __syncthreads();
+  const int Nemit = sNemit;
+  if (Nemit > 0) {
+    // no push block binned this step's emitted electrons (the diode has no
+    // electron in flight): their charge is added here
+    Hist h;
+    h.h3 = reinterpret_cast<unsigned*>(rho_s + nn);
+    hist_zero(h, ic.Nz);
+    __syncthreads();
+    for (int base = 0; base < Nemit; base += nt) {
+      const int k = base + tid;
+      float zz[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      unsigned am = 0u;
+      if (k < Nemit) {
+        float vx, vy, vz;
+        emitted_electron(ic, k, step, zz[0], vx, vy, vz);
+        am = 1u;
+      }
+      deposit_warp(h, zz, am, ic.inv_dz_f, ic.Nz, true);
+    }
+    __syncthreads();
+    for (int j = tid; j < nn; j += nt) rho_s[j] -= hist_node(h, j, ic.Nz);
+    __syncthreads();
+  }
+  for (int j = tid; j < nn; j += nt) st.rho[off + j] = rho_s[j];
   const bool sample = profile_due(st.prof_period, ic.window_start, step);
   field_solve(ic, rho_s, st.E + off, sample ? st.phi + off : nullptr, ws64);
   if (sample) {
@@ -1003,7 +1031,12 @@ __device__ void mid_absorbed(const DevState& st, int g, unsigned char* smem, int
   const long long Sg = st.part[g];
   long long* blo = reinterpret_cast<long long*>(smem);               // [Geff + 1]
   int* bpre = reinterpret_cast<int*>(blo + Geff + 1);                // [Geff + 1]
-  for (int b = tid; b <= Geff; b += nt) blo[b] = st.bstart[b];
+  // block starts and absorbed counts in one pass (a count is used only where
+  // the block overlaps the segment)
+  for (int b = tid; b <= Geff; b += nt) {
+    blo[b] = st.bstart[b];
+    bpre[b] = b < Geff ? st.dcount[(long long)g * st.G + b] : 0;
+  }
   __syncthreads();
   int carry = 0;
   for (int base = 0; base < Geff; base += nt) {
@@ -1011,8 +1044,9 @@ __device__ void mid_absorbed(const DevState& st, int g, unsigned char* smem, int
     int c = 0;
     if (b < Geff) {
       const long long lb = blo[b], hb = blo[b + 1];
-      if (qg > 0 && lb < hb && lb < Sg + qg && hb > Sg) c = st.dcount[(long long)g * st.G + b];
+      if (qg > 0 && lb < hb && lb < Sg + qg && hb > Sg) c = bpre[b];
     }
+    __syncthreads();                   // bpre is overwritten with the prefix below
     int tot;
     const int ex = block_exclusive_scan<int>(c, &tot, ws32);
     if (b < Geff) bpre[b] = carry + ex;
@@ -1054,8 +1088,8 @@ __device__ void mid_absorbed(const DevState& st, int g, unsigned char* smem, int
 }
 
 // Blocks [0, n_inst): field of diode b.  [n_inst, 4 n_inst): absorbed list
-// and tallies of segment b - n_inst.  The rest: the candidates' collisions
-// (the first of them also re-weights the push blocks for the next step).
+// and tallies of segment b - n_inst.  Block 4 n_inst: re-weights the push
+// blocks for the next step.  The rest: the candidates' collisions.
 __global__ void __launch_bounds__(kPostThreads, 2) k_mid(DevState st) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long wsl[64];
@@ -1067,14 +1101,12 @@ __global__ void __launch_bounds__(kPostThreads, 2) k_mid(DevState st) {
     mid_field(st, b, smem, ws64);
   } else if (b < 4 * ni) {
     mid_absorbed(st, b - ni, smem, ws32, wsl, wsd);
+  } else if (b == 4 * ni) {
+    update_push_weights(st, (int)st.part[st.n_seg + 1], reinterpret_cast<float*>(wsd), ws64);
   } else {
-    const int m = b - 4 * ni;
+    const int m = b - 4 * ni - 1;
     mcc_candidates(st, (unsigned)m * blockDim.x + threadIdx.x,
-                   (unsigned)(gridDim.x - 4 * ni) * blockDim.x);
-    if (m == 0) {
-      __syncthreads();
-      update_push_weights(st, (int)st.part[st.n_seg + 1], reinterpret_cast<float*>(wsd), ws64);
-    }
+                   (unsigned)(gridDim.x - 4 * ni - 1) * blockDim.x);
   }
 }
 
@@ -1089,7 +1121,7 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post(DevState st) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int ws32[32];
   __shared__ InstConst ic;
-  __shared__ int sE, sNemit, sLast, sD, sN, sDi;
+  __shared__ int sE, sNemit, sLast, sDi;
 
   const int inst = blockIdx.x / 3, sp = blockIdx.x - 3 * inst;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -1107,6 +1139,11 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post(DevState st) {
   PostScratch* ps = st.post + inst;
   const long long step = dyn->step;
   const uint32_t base_id = dyn->next_id;
+  // every thread reads the counts itself (in the round trip of the constants)
+  const int D = ps->D[sp], N = ps->N[sp];
+  const int g = inst * 3 + sp;
+  const long long off = st.seg_off[g];
+  const int cap = st.seg_cap[g];
   if (tid == 0) {
     int e = dyn->ev_count;
     if (e > kEvCap) {
@@ -1114,28 +1151,22 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post(DevState st) {
       e = kEvCap;
     }
     sE = e;
-    sD = ps->D[sp];
-    sN = ps->N[sp];
     sDi = ps->D[2];
   }
-  __syncthreads();                 // ic and the counts are read by every thread below
+  // the ordered absorbed list, staged in shared memory when it fits
+  uint32_t* dd = st.dead_buf + off;
+  if (D <= kDeadSmem) {
+    uint32_t* dd_s = reinterpret_cast<uint32_t*>(smem);
+    for (int k = tid; k < D; k += nt) dd_s[k] = dd[k];
+    dd = dd_s;
+  }
+  __syncthreads();                 // ic, the counts and the list are read by every thread below
   if (tid == 0) sNemit = emitted_count(ic, step);
 
   // ---- hole filling: the dead slots below the new count take the live
   // particles above it, in order
-  const int g = inst * 3 + sp;
-  const long long off = st.seg_off[g];
-  const int cap = st.seg_cap[g];
-  const int D = sD, N = sN;
   const int Nn = N - D;
   {
-    uint32_t* dd = st.dead_buf + off;
-    if (D <= kDeadSmem) {
-      uint32_t* dd_s = reinterpret_cast<uint32_t*>(smem);
-      for (int k = tid; k < D; k += nt) dd_s[k] = dd[k];
-      dd = dd_s;
-    }
-    __syncthreads();
     int lo = 0, hi = D;
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
