@@ -196,7 +196,8 @@ int pic_inject(pic_handle* h, int instance, int species, int64_t n, const float*
 int pic_step(pic_handle* h, int64_t n_steps);
 
 /* Same steps as pic_step, launched one by one with CUDA events around each
- * kernel; synchronises and reports per-kernel device time. */
+ * kernel; synchronises and reports per-kernel device time (each kernel's
+ * time includes its launch latency, which graphs hide in pic_step). */
 int pic_profile_steps(pic_handle* h, int64_t n_steps, pic_profile* out);
 
 /* Window tallies and Eq. 1-8 diagnostics of one instance.  Synchronises. */

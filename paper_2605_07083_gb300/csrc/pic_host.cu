@@ -262,6 +262,7 @@ cudaError_t raise_smem_limits(int device) {
                        (const void*)k_mid};
   for (const void* f : fns) {
     e = set_dynamic_smem_limit(f, optin);
+
     if (e != cudaSuccess) return e;
   }
   e = sort_prepare(optin);
@@ -805,7 +806,6 @@ int pic_profile_steps(pic_handle* h, int64_t n_steps, pic_profile* out) {
   cudaEvent_t t0, t1;
   cudaEventCreate(&t0);
   cudaEventCreate(&t1);
-  std::vector<int32_t> counts;
   cudaEventRecord(t0, h->stream);
   std::vector<int> sorted(n_steps, 0);
   for (int64_t i = 0; i < n_steps; ++i) {
@@ -853,7 +853,6 @@ int pic_profile_steps(pic_handle* h, int64_t n_steps, pic_profile* out) {
   for (auto& x : ev) cudaEventDestroy(x);
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
-  (void)counts;
   return check_flags(h);
 }
 

@@ -421,6 +421,25 @@ __device__ __forceinline__ void push_quad(const SegCtx& c, const float2* Es2, fl
   cm = m;
 }
 
+// Chunk ch of a warp's quads [wq0, wq1) of a segment at slot off: its z,
+// v_z and id into stage ch & 1 of the warp, completing on that stage's
+// mbarrier.  Issued by one lane.
+__device__ __forceinline__ void issue_chunk(const DevState& st, unsigned char* wstage,
+                                            unsigned long long* wbar, long long off, int wq0,
+                                            int wq1, int ch) {
+  const int s = ch & 1;
+  const int qc = wq0 + 32 * ch;
+  const int nq = (wq1 - qc) < 32 ? (wq1 - qc) : 32;
+  const uint32_t bytes = (uint32_t)nq * 16u;
+  unsigned char* b = wstage + s * kStageBytes;
+  const long long at = off + 4LL * qc;
+  fence_proxy_async();
+  mbar_expect_tx(&wbar[s], 3u * bytes);
+  bulk_g2s(b, st.z + at, bytes, &wbar[s]);
+  bulk_g2s(b + 512, st.vz + at, bytes, &wbar[s]);
+  bulk_g2s(b + 1024, st.id + at, bytes, &wbar[s]);
+}
+
 template <bool kDepositOnly>
 __device__ __forceinline__ void push_body(const DevState& st) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -496,6 +515,20 @@ __device__ __forceinline__ void push_body(const DevState& st) {
     const int inst = g / 3, sp = g - 3 * inst;
     const long long sgn = (sp == 2) ? 1LL : -1LL;
     __syncthreads();
+    // quads of this block, relative to the segment: 32-bit (a segment holds
+    // < 2^31 particles); taken kSubQuads at a time, each sub-range binned
+    // and flushed on its own so that no counter of the histogram overflows
+    const int q0 = (int)((lo > s0 ? lo : s0) - s0);
+    const int q1 = (int)((hi < s1 ? hi : s1) - s0);
+    const long long off = st.seg_off[g];
+    if (!kDepositOnly && lane == 0) {
+      // the warp's first two chunks are in flight while the block stages
+      // the diode's constants and field
+      const int b0 = (q1 - q0 > kSubQuads) ? q0 + kSubQuads : q1;
+      const int pw0 = (int)warp_start(q0, b0, warp, W), pw1 = (int)warp_start(q0, b0, warp + 1, W);
+      if (pw1 > pw0) issue_chunk(st, wstage, wbar, off, pw0, pw1, 0);
+      if (pw1 - pw0 > 32) issue_chunk(st, wstage, wbar, off, pw0, pw1, 1);
+    }
     if (inst != cur) {
       {
         const int* src = reinterpret_cast<const int*>(st.ic + inst);
@@ -512,11 +545,6 @@ __device__ __forceinline__ void push_body(const DevState& st) {
       }
       cur = inst;
     }
-    // quads of this block, relative to the segment: 32-bit (a segment holds
-    // < 2^31 particles); taken kSubQuads at a time, each sub-range binned
-    // and flushed on its own so that no counter of the histogram overflows
-    const int q0 = (int)((lo > s0 ? lo : s0) - s0);
-    const int q1 = (int)((hi < s1 ? hi : s1) - s0);
     int dead_total = 0;                // absorbed slots the block listed for this segment
     for (int a = q0; a < q1; a += kSubQuads) {
       const int b1 = (q1 - a > kSubQuads) ? a + kSubQuads : q1;
@@ -542,11 +570,9 @@ __device__ __forceinline__ void push_body(const DevState& st) {
         if (threadIdx.x == 0) st.dyn[inst].emit_dep = 1;
       }
       const int wq0 = (int)warp_start(a, b1, warp, W), wq1 = (int)warp_start(a, b1, warp + 1, W);
-      const long long off = st.seg_off[g];
       const int N = st.seg_count[g];
       float* __restrict__ zp = st.z + off;
       float* __restrict__ vzp = st.vz + off;
-      const uint32_t* __restrict__ idp = st.id + off;
       const float inv_dz = icS.inv_dz_f;
       const int Nz = icS.Nz;
       const bool agg = st.agg != 0;
@@ -568,21 +594,9 @@ __device__ __forceinline__ void push_body(const DevState& st) {
       // chunk ch of this warp = quads [wq0 + 32 ch, +32); bulk copies run two
       // chunks ahead of the compute
       const int nchunks = (int)((wq1 - wq0 + 31) >> 5);
-      auto issue = [&](int ch) {
-        const int s = ch & 1;
-        const int qc = wq0 + 32 * ch;
-        const int nq = (wq1 - qc) < 32 ? (wq1 - qc) : 32;
-        const uint32_t bytes = (uint32_t)nq * 16u;
-        unsigned char* b = wstage + s * kStageBytes;
-        fence_proxy_async();
-        mbar_expect_tx(&wbar[s], 3u * bytes);
-        bulk_g2s(b, zp + 4 * qc, bytes, &wbar[s]);
-        bulk_g2s(b + 512, vzp + 4 * qc, bytes, &wbar[s]);
-        bulk_g2s(b + 1024, idp + 4 * qc, bytes, &wbar[s]);
-      };
-      if (!kDepositOnly && lane == 0) {
-        if (nchunks > 0) issue(0);
-        if (nchunks > 1) issue(1);
+      if (!kDepositOnly && lane == 0 && a != q0) {   // the first sub-range's are issued
+        if (nchunks > 0) issue_chunk(st, wstage, wbar, off, wq0, wq1, 0);
+        if (nchunks > 1) issue_chunk(st, wstage, wbar, off, wq0, wq1, 1);
       }
       int ch = 0;
       for (int base = wq0; base < wq1; base += 32, ++ch) {
@@ -612,7 +626,7 @@ __device__ __forceinline__ void push_body(const DevState& st) {
             id4s = reinterpret_cast<const uint4*>(b + 1024)[lane];
           }
           __syncwarp();
-          if (lane == 0 && ch + 2 < nchunks) issue(ch + 2);
+          if (lane == 0 && ch + 2 < nchunks) issue_chunk(st, wstage, wbar, off, wq0, wq1, ch + 2);
         }
         if (base + 32 <= wq1 && 4 * (base + 32) <= N) {
           // every lane holds four live particles (warp-uniform): straight-line
