@@ -341,17 +341,32 @@ def cpu_baseline_batched(n_steps=16):
                       "start-up)" % (n_steps, wall)}
 
 
-def run_batched(steps=100, warmup=20):
-    """Speed-up of one batched handle over the same diodes run one by one."""
+def run_batched(steps=10_000, warmup=200, tune_steps=400):
+    """The 64-diode sweep for 10,000 steps: one batched handle (tuned by the
+    autotuner on a copy of the job first) against the same diodes run one
+    after another on their own handles with the default shape.  Results do
+    not depend on the launch shape, so every diode's wall tallies must come
+    out identical both ways."""
     import torch
     from paper_2605_07083_gb300 import pic
-    from paper_2605_07083_gb300.autotune import autotune
+    from paper_2605_07083_gb300 import autotune as A
     ps, states = batched_workload(steps=steps)
     n_tot = sum(s[0].size for s in states)
-    d = pic.Diode(ps)
-    for i, st in enumerate(states):
-        d.inject(0, *st, instance=i)
-    tuning = autotune(d, steps=10)
+
+    def make():
+        h = pic.Diode(ps)
+        for i, st in enumerate(states):
+            h.inject(0, *st, instance=i)
+        return h
+
+    t0 = time.perf_counter()
+    d = make()
+    tuning = A.autotune(d, steps=tune_steps)
+    d.close()
+    del d
+    tune_s = time.perf_counter() - t0
+    d = make()
+    A.apply(d, tuning)
     d.step(warmup)
     d.synchronize()
     p0 = sum(d.diagnostics(i)["particles_pushed"] for i in range(len(ps)))
@@ -361,11 +376,12 @@ def run_batched(steps=100, warmup=20):
     e1.record(d.stream)
     e1.synchronize()
     ms_b = e0.elapsed_time(e1)
-    pushed_b = sum(d.diagnostics(i)["particles_pushed"] for i in range(len(ps))) - p0
+    diag_b = [d.diagnostics(i) for i in range(len(ps))]
+    pushed_b = sum(x["particles_pushed"] for x in diag_b) - p0
     d.close()
     del d
-    ms_seq, pushed_s = 0.0, 0
-    for p, st in zip(ps, states):
+    ms_seq, pushed_s, same = 0.0, 0, 0
+    for i, (p, st) in enumerate(zip(ps, states)):
         s1 = pic.Diode(p)
         s1.inject(0, *st)
         s1.step(warmup)
@@ -377,14 +393,36 @@ def run_batched(steps=100, warmup=20):
         b.record(s1.stream)
         b.synchronize()
         ms_seq += a.elapsed_time(b)
-        pushed_s += s1.diagnostics()["particles_pushed"] - q0
+        dg = s1.diagnostics()
+        pushed_s += dg["particles_pushed"] - q0
+        same += int(np.array_equal(dg["count"], diag_b[i]["count"])
+                    and dg["emitted"] == diag_b[i]["emitted"]
+                    and np.array_equal(dg["n_live"], diag_b[i]["n_live"]))
         s1.close()
-    return {"instances": len(ps), "particles_initial": int(n_tot), "steps": steps,
+    bf = np.array([x["backflow_ratio"] for x in diag_b], np.float64)
+    gam = np.array([p["gamma_emit"] for p in ps], np.float64)
+    ok = np.isfinite(bf)
+    return {"instances": len(ps), "particles_initial": int(n_tot),
+            "particles_final": int(sum(int(np.sum(x["n_live"])) for x in diag_b)),
+            "steps": steps, "warmup": warmup,
             "ms_per_step_batched": ms_b / steps, "ms_per_step_sequential": ms_seq / steps,
             "speedup": ms_seq / ms_b,
             "value_batched": pushed_b / (ms_b * 1e-3), "value_sequential": pushed_s / (ms_seq * 1e-3),
             "unit": "particle-steps/s",
-            "tuning": {k: tuning[k] for k in ("push_threads", "push_blocks_per_sm", "sort_period")},
+            "instances_with_identical_tallies": same,
+            "launch": "one CUDA graph per %d steps, 3 kernels per step (push, mid, post) "
+                      "over all 64 diodes" % A.graph_length(tuning["graph_steps"],
+                                                            tuning["sort_period"]),
+            "tuning": {k: tuning[k] for k in ("push_threads", "sort_period", "graph_steps",
+                                              "ms_per_step")},
+            "autotune": {"trials": len(tuning["trials"]), "timed_steps_per_trial": tune_steps,
+                         "seconds": tune_s,
+                         "grid": "threads 128..384 step 32 x sort period {0,25,50,100,200} "
+                                 "x graph steps {16,64,256} (rounded to whole sort periods)"},
+            "backflow_ratio_window": {"min": float(bf[ok].min()) if ok.any() else None,
+                                      "max": float(bf[ok].max()) if ok.any() else None,
+                                      "corr_with_gamma": float(np.corrcoef(gam[ok], bf[ok])[0, 1])
+                                      if ok.sum() > 2 else None},
             "workload": "64 He diodes: Gamma U[5,9]e19, gap U[1,5] mm (cells = gap/2.5 um), "
                         "n_He logU[1e21,1e22], 5e4-4e6 emitted e preloaded (log-uniform), 10 V"}
 

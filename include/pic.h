@@ -112,15 +112,20 @@ typedef struct pic_tuning {
     uint32_t size;            /* sizeof(pic_tuning) */
     int32_t push_threads;     /* threads per block of the particle kernels (64..384, multiple of
                                  32; default: the size that keeps closest to 24 resident warps
-                                 per SM for the handle's cell count, 256 when that ties) */
+                                 per SM for the handle's cell count, the first of 384, 256,
+                                 128, 160, ... that does) */
     int32_t push_blocks_per_sm;  /* cap on resident blocks per SM (default: occupancy limit) */
     int32_t sort_period;      /* counting sort by cell every this many steps; < 0 disables */
-    int32_t graph_steps;      /* longest step loop captured as one CUDA graph (default 64);
-                                 every power of two below it is captured too, so pic_step(n)
-                                 runs any n as graphs.  With a periodic sort only the
-                                 full-length graph exists and runs on sort-aligned steps.
-                                 All of them are built by the first pic_step after a change
-                                 of launch shape.  < 0 disables graphs */
+    int32_t graph_steps;      /* longest step loop captured as one CUDA graph (default 64,
+                                 at most 4096); every power of two below it is captured too,
+                                 so pic_step(n) runs any n as graphs.  With a periodic sort
+                                 the longest graph is rounded up to a multiple of the sort
+                                 period, the shorter ones are the period times powers of two,
+                                 and graphs start on sort-aligned steps only: pic_step runs
+                                 single steps up to the next aligned step and for a remainder
+                                 shorter than one period (no graphs at all when the period
+                                 exceeds 4096).  All of them are built by the first pic_step
+                                 after a change of launch shape.  < 0 disables graphs */
     int32_t wait_polls;       /* polls of a bulk-copy wait in the push kernel before it gives
                                  up with PIC_ETIMEOUT (default 2^20, each suspending the warp
                                  up to ~1 us): n > 0 sets n; -1 gives up without polling, a

@@ -71,8 +71,8 @@ struct pic_handle {
   int sticky = PIC_OK;
   int64_t host_step = 0;        // mirror of the device step counter
   int64_t last_sort_step = 0;
-  // captured step loops, longest first: graph_steps steps, then every power
-  // of two below it, so that any step count runs as graphs
+  // captured step loops, longest first (build_graphs), so that any step
+  // count runs as graphs
   std::vector<std::pair<int, cudaGraphExec_t>> graphs;
   size_t push_smem = 0, post_smem = 0, field_smem = 0, mid_smem = 0;
   size_t dcount_ints = 0;
@@ -319,20 +319,23 @@ int set_launch_shape(pic_handle* h) {
     h->dcount_ints = need;
   }
   // push-block weights back to equal shares; their times unknown
+  // layout: bwp [G + 1] long long, bw [G] int, bt [G] int, bw_n [2] int
+  const size_t bw_bytes = sizeof(long long) * (size_t)(2 * h->G + 2);
   if (h->G > h->bw_len) {
-    void* p = dev_alloc(h, sizeof(long long) * (size_t)(h->G + 1) + sizeof(int) * 2 * (size_t)h->G);
+    void* p = dev_alloc(h, bw_bytes);
     if (!p) return PIC_ENOMEM;
     h->st.bwp = (long long*)p;
     h->bw_len = h->G;
   }
   h->st.bw = (int*)(h->st.bwp + h->G + 1);
   h->st.bt = h->st.bw + h->G;
+  h->st.bw_n = h->st.bt + h->G;
   {
-    std::vector<long long> w((size_t)h->G + 1 + h->G, 0);
+    std::vector<long long> w((size_t)2 * h->G + 2, 0);
     for (int b = 0; b <= h->G; ++b) w[b] = (long long)b * kNominalWeight;
     int* wi = reinterpret_cast<int*>(w.data() + h->G + 1);
     for (int b = 0; b < h->G; ++b) wi[b] = kNominalWeight;
-    const size_t bytes = sizeof(long long) * (size_t)(h->G + 1) + sizeof(int) * 2 * (size_t)h->G;
+    const size_t bytes = bw_bytes;
     cudaError_t e2 = cudaMemcpyAsync(h->st.bwp, w.data(), bytes, cudaMemcpyHostToDevice, h->stream);
     if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(h->stream);
     if (e2 != cudaSuccess) return cuda_fail(h, e2);
@@ -429,10 +432,12 @@ cudaError_t launch_step(pic_handle* h) {
   return cudaGetLastError();
 }
 
+// Captures len steps.  With a periodic sort the graph is only ever launched
+// on a sort-aligned step, so the sorts sit after every sort_period-th step of
+// it counted from its start.
 int build_graph(pic_handle* h, int len, cudaGraphExec_t* out) {
   *out = nullptr;
   cudaGraph_t g = nullptr;
-  const int64_t saved = h->host_step;
   cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail_at(h, e, "cudaStreamBeginCapture");
   for (int i = 0; i < len; ++i) {
@@ -440,7 +445,7 @@ int build_graph(pic_handle* h, int len, cudaGraphExec_t* out) {
     k_mid<<<4 * h->n_inst + h->mcc_blocks, kPostThreads, h->mid_smem, h->stream>>>(h->st);
     k_post<<<3 * h->n_inst, kPostThreads, h->post_smem, h->stream>>>(h->st);
     launch_profile(h);
-    if (sort_due(h, saved + i + 1)) launch_sort(h);
+    if (sort_due(h, i + 1)) launch_sort(h);
   }
   e = cudaStreamEndCapture(h->stream, &g);
   if (e != cudaSuccess) return cuda_fail_at(h, e, "cudaStreamEndCapture");
@@ -453,19 +458,33 @@ int build_graph(pic_handle* h, int len, cudaGraphExec_t* out) {
   return PIC_OK;
 }
 
+// Length of the longest step graph: graph_steps, at most kMaxGraphSteps,
+// rounded up to a multiple of the sort period when there is one; 0 (no
+// graphs) when graphs are off or a sort period is longer than the cap.
+constexpr int kMaxGraphSteps = 4096;
+int graph_unit(const pic_handle* h) {
+  if (h->graph_steps <= 0) return 0;
+  const int64_t want = std::min(h->graph_steps, kMaxGraphSteps);
+  if (h->sort_period <= 0) return (int)want;
+  const int64_t sp = h->sort_period;
+  const int64_t len = (want + sp - 1) / sp * sp;
+  return len <= kMaxGraphSteps ? (int)len : 0;
+}
+
 // All step graphs of the handle at once (the first pic_step after a change
-// of launch shape pays for them): graph_steps steps, and 2^k steps for every
-// 2^k < graph_steps.  With a periodic sort only the full-length graph is
-// built; it is launched on sort-aligned steps only.
+// of launch shape pays for them): the longest (graph_unit), then u * 2^k for
+// every u * 2^k below it, u = 1 without a sort and u = sort_period with one.
+// pic_step then runs any step count as graphs, less at most sort_period - 1
+// single steps on each side when a sort is on.
 int build_graphs(pic_handle* h) {
   drop_graph(h);
-  std::vector<int> lens{h->graph_steps};
-  if (h->sort_period <= 0) {
-    int p2 = 1;
-    while (p2 * 2 < h->graph_steps) p2 *= 2;
-    for (; p2 >= 1; p2 /= 2)
-      if (p2 < h->graph_steps) lens.push_back(p2);
-  }
+  const int top = graph_unit(h);
+  const int unit = h->sort_period > 0 ? h->sort_period : 1;
+  std::vector<int> lens{top};
+  int64_t p = unit;
+  while (p * 2 < top) p *= 2;
+  for (; p >= unit; p /= 2)
+    if (p < top) lens.push_back((int)p);
   for (int len : lens) {
     cudaGraphExec_t g = nullptr;
     int rc = build_graph(h, len, &g);
@@ -768,18 +787,23 @@ int pic_step(pic_handle* h, int64_t n_steps) {
   int rc = ensure_field(h);
   if (rc != PIC_OK) return rc;
   int64_t left = n_steps;
-  const int len = h->graph_steps;
-  // a captured graph bakes in where the periodic sort falls: with a sort,
-  // only sort-aligned starts with a sort-aligned length run as a graph
-  const bool aligned = h->sort_period <= 0 ||
-                       (len % h->sort_period == 0 && h->host_step % h->sort_period == 0);
-  if (len > 0 && aligned && (h->sort_period <= 0 || left >= len)) {
+  const int len = graph_unit(h);
+  const int64_t sp = h->sort_period;
+  // a graph bakes in where the periodic sort falls, so with a sort the graphs
+  // start on sort-aligned steps: single steps up to the next aligned one
+  if (len > 0 && sp > 0) {
+    for (; left > 0 && h->host_step % sp != 0; --left) {
+      cudaError_t e = launch_step(h);
+      if (e != cudaSuccess) return cuda_fail_at(h, e, "step kernel launch");
+    }
+  }
+  if (len > 0 && left > 0) {
     if (h->graphs.empty() || h->graphs[0].first != len) {
       rc = build_graphs(h);
       if (rc != PIC_OK) return rc;
     }
-    // longest first: n steps run as floor(n / graph_steps) full graphs and
-    // the binary digits of the rest
+    // longest first: n steps run as floor(n / len) full graphs and the
+    // binary digits of the rest (in sort periods when there is a sort)
     for (const auto& g : h->graphs) {
       while (left >= g.first) {
         cudaError_t e = cudaGraphLaunch(g.second, h->stream);

@@ -14,6 +14,7 @@ constexpr int kPostThreads = 512;
 constexpr int kHistMaxParticles = (1 << 20) - 256;
 // push-block weights (shares of the particle range): nominal, bounds
 constexpr int kNominalWeight = 1024, kMinWeight = 256, kMaxWeight = 4096;
+constexpr int kWeightJumps = 3;    // weight updates that take the measured shares outright
 // quads a push block bins before it flushes its histogram
 constexpr int kSubQuads = kHistMaxParticles / 4;
 constexpr long long kMaxSlots = 1LL << 29;            // particle slots per handle
@@ -139,6 +140,7 @@ struct DevState {
   int* bw;                 // [G] push-block weights: each block's share of the particles
   long long* bwp;          // [G + 1] their prefix sums (the block ranges are Q bwp[b] / bwp[G])
   int* bt;                 // [G] streaming time of each block in the last push, ns
+  int* bw_n;               // [1] weight updates since the last reset to equal shares
   int agg;
 };
 

@@ -855,11 +855,15 @@ __device__ void update_push_weights(const DevState& st, int G, float* ws, long l
   n = block_sum<float>(n, ws);
   if (n <= 0.0f || !(r_sum > 0.0f)) return;
   const float mean = r_sum / n;
+  // the first updates after a reset jump to the measured shares; later ones
+  // move halfway, which damps the step-to-step noise of the block times
+  const int n_upd = *st.bw_n;
+  const float keep = n_upd < kWeightJumps ? 0.0f : 0.5f;
   for (int b = threadIdx.x; b < G; b += blockDim.x) {
     const int t = st.bt[b];
     if (t <= 0) continue;
     const float target = (float)kNominalWeight * ((float)st.bw[b] / (float)t) / mean;
-    const float w = 0.5f * ((float)st.bw[b] + target);
+    const float w = keep * (float)st.bw[b] + (1.0f - keep) * target;
     st.bw[b] = (int)fminf(fmaxf(rintf(w), (float)kMinWeight), (float)kMaxWeight);
   }
   __syncthreads();
@@ -872,7 +876,10 @@ __device__ void update_push_weights(const DevState& st, int G, float* ws, long l
     if (b < st.G) st.bwp[b + 1] = carry + ex + w;
     carry += tot;
   }
-  if (threadIdx.x == 0) st.bwp[0] = 0;
+  if (threadIdx.x == 0) {
+    st.bwp[0] = 0;
+    if (n_upd < kWeightJumps) *st.bw_n = n_upd + 1;
+  }
 }
 
 // ------------------------------------------------------------------ k_mid / k_post

@@ -280,6 +280,58 @@ def test_periodic_sort_leaves_the_physics_bit_identical(env):
     np.testing.assert_allclose(d0["ke"], d1["ke"], rtol=1e-12)
 
 
+def test_sort_steps_are_the_same_with_and_without_graphs(env):
+    """A sort period that does not divide graph_steps (7 and 16: the graphs
+    become 21 and 7 steps long) and step counts that start off the sort
+    phase: the raw array order, which shows where every sort fell, and the
+    charge match a run of single launches with the same period."""
+    pic, O = env
+    p = W.single_diode_small()
+    p["n_gas"] = 2e22
+    state = mixed_state(p, 23, 20000, 8000)
+    runs = []
+    for graphs in (-1, 16):
+        d = pic.Diode(p)
+        for sp in range(3):
+            d.inject(sp, *state[sp])
+        d.tune(sort_period=7, graph_steps=graphs)
+        rhos = []
+        for n in (3, 50, 1, 66, 29):
+            d.step(n)
+            rhos.append(d.rho_fixed())
+        runs.append((rhos, [d.state(sp) for sp in range(3)], d.diagnostics()))
+        d.close()
+    (ra, sa, da), (rb, sb, db) = runs
+    for x, y in zip(ra, rb):
+        assert np.array_equal(x, y)
+    for a, b in zip(sa, sb):
+        for k in a:
+            assert np.array_equal(a[k], b[k]), k
+    assert da["step"] == db["step"] == 149
+    assert np.array_equal(da["count"], db["count"])
+
+
+def test_autotuner_times_its_grid_and_keeps_the_fastest(env):
+    """The autotuner on a reduced grid: one trial per distinct graph length,
+    each timed over whole sort periods, and the handle left on the fastest
+    shape, which still steps."""
+    pic, O = env
+    from paper_2605_07083_gb300 import autotune as A
+    p = W.single_diode_small()
+    d = pic.Diode(p)
+    d.inject(0, *mixed_state(p, 5, 20000, 10)[0])
+    res = A.autotune(d, steps=50, settle=10, threads=(128, 384), sort_periods=(0, 25),
+                     graph_steps=(16, 20, 64))
+    # sort period 25 rounds 16 and 20 up to 25 and 64 up to 75
+    assert len(res["trials"]) == 2 * (3 + 2)
+    assert res["ms_per_step"] == min(t["ms_per_step"] for t in res["trials"])
+    assert all(t["ms_per_step"] > 0 for t in res["trials"])
+    s0 = d.diagnostics()["step"]
+    d.step(30)
+    assert d.diagnostics()["step"] == s0 + 30
+    d.close()
+
+
 def test_production_determinism_over_many_steps(env):
     """The 2048-cell production diode (a 2.6M-particle preload of the same
     recipe): two runs give identical fixed-point charge at steps 1, 100 and
