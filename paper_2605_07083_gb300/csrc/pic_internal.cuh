@@ -311,7 +311,9 @@ __device__ __forceinline__ unsigned frac_units(float f) {
 
 // ---------------------------------------------------------------- bulk copies
 // 1D bulk copies global -> shared completing on an mbarrier (sm_90+ PTX).
-constexpr int kStageBytes = 1536;     // one warp chunk: 128 x (z, v_z, id)
+constexpr int kChunkQuads = 64;       // quads of one warp chunk (two per lane)
+constexpr int kArrBytes = kChunkQuads * 16;   // one array of a chunk
+constexpr int kStageBytes = 3 * kArrBytes;    // one warp chunk: (z, v_z, id)
 constexpr int kWaitLimit = 1 << 20;   // bounded polls (each suspends up to kSuspendNs)
 constexpr uint32_t kSuspendNs = 1000;
 

@@ -428,16 +428,74 @@ __device__ __forceinline__ void issue_chunk(const DevState& st, unsigned char* w
                                             unsigned long long* wbar, long long off, int wq0,
                                             int wq1, int ch) {
   const int s = ch & 1;
-  const int qc = wq0 + 32 * ch;
-  const int nq = (wq1 - qc) < 32 ? (wq1 - qc) : 32;
+  const int qc = wq0 + kChunkQuads * ch;
+  const int nq = (wq1 - qc) < kChunkQuads ? (wq1 - qc) : kChunkQuads;
   const uint32_t bytes = (uint32_t)nq * 16u;
   unsigned char* b = wstage + s * kStageBytes;
   const long long at = off + 4LL * qc;
   fence_proxy_async();
   mbar_expect_tx(&wbar[s], 3u * bytes);
   bulk_g2s(b, st.z + at, bytes, &wbar[s]);
-  bulk_g2s(b + 512, st.vz + at, bytes, &wbar[s]);
-  bulk_g2s(b + 1024, st.id + at, bytes, &wbar[s]);
+  bulk_g2s(b + kArrBytes, st.vz + at, bytes, &wbar[s]);
+  bulk_g2s(b + 2 * kArrBytes, st.id + at, bytes, &wbar[s]);
+}
+
+// Wait for stage s of the warp's chunk ch.  If the copy does not complete in
+// time: flag it, let this warp's copies in flight (this stage and the next)
+// land with the full limit, keep the stage parities in step and return
+// false, so that the warp stops its part of the segment.
+__device__ __forceinline__ bool stage_ready(const DevState& st, unsigned long long* wbar,
+                                            unsigned& phase, int s, int ch, int nchunks,
+                                            int inst, int lane) {
+  const bool arrived = mbar_wait_bounded(&wbar[s], (phase >> s) & 1u, st.wait_limit);
+  if (!__all_sync(0xffffffffu, arrived)) {
+    if (lane == 0) atomicOr(&st.dyn[inst].err, ERR_TIMEOUT);
+    if (mbar_wait_bounded(&wbar[s], (phase >> s) & 1u)) phase ^= 1u << s;
+    if (ch + 1 < nchunks && mbar_wait_bounded(&wbar[s ^ 1], (phase >> (s ^ 1)) & 1u))
+      phase ^= 1u << (s ^ 1);
+    return false;
+  }
+  phase ^= 1u << s;
+  return true;
+}
+
+// Collision candidates -> the compact global list (one atomic per warp);
+// absorbed slots -> this warp's ordered list (warp scans).  Called by all 32
+// lanes for a chunk in which some lane has either; q is the lane's quad.
+__device__ __forceinline__ void record_events(const DevState& st, int g, int inst, int q,
+                                              unsigned cm, unsigned dm, uint32_t* dbuf,
+                                              int& dead_run, int lane) {
+  const int cc = __popc(cm), dc = __popc(dm);
+  int ci = cc, di = dc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int yc = __shfl_up_sync(0xffffffffu, ci, o);
+    const int yd = __shfl_up_sync(0xffffffffu, di, o);
+    if (lane >= o) { ci += yc; di += yd; }
+  }
+  const int ctot = __shfl_sync(0xffffffffu, ci, 31);
+  const int dtot = __shfl_sync(0xffffffffu, di, 31);
+  if (ctot) {
+    unsigned cbase = 0;
+    if (lane == 0) cbase = atomicAdd(st.cand_count, (unsigned)ctot);
+    cbase = __shfl_sync(0xffffffffu, cbase, 0);
+    unsigned w = cbase + (unsigned)(ci - cc);
+    for (int k2 = 0; k2 < 4; ++k2) {
+      if (cm & (1u << k2)) {
+        if (w < (unsigned)st.cand_cap)
+          st.cand_buf[w] = ((unsigned long long)g << 32) | (unsigned long long)(4 * q + k2);
+        else
+          atomicOr(&st.dyn[inst].err, ERR_CAPACITY);
+        ++w;
+      }
+    }
+  }
+  if (dtot) {
+    int w = dead_run + di - dc;
+    for (int k2 = 0; k2 < 4; ++k2)
+      if (dm & (1u << k2)) dbuf[w++] = (uint32_t)(4 * q + k2);
+    dead_run += dtot;
+  }
 }
 
 template <bool kDepositOnly>
@@ -527,7 +585,7 @@ __device__ __forceinline__ void push_body(const DevState& st) {
       const int b0 = (q1 - q0 > kSubQuads) ? q0 + kSubQuads : q1;
       const int pw0 = (int)warp_start(q0, b0, warp, W), pw1 = (int)warp_start(q0, b0, warp + 1, W);
       if (pw1 > pw0) issue_chunk(st, wstage, wbar, off, pw0, pw1, 0);
-      if (pw1 - pw0 > 32) issue_chunk(st, wstage, wbar, off, pw0, pw1, 1);
+      if (pw1 - pw0 > kChunkQuads) issue_chunk(st, wstage, wbar, off, pw0, pw1, 1);
     }
     if (inst != cur) {
       {
@@ -591,64 +649,83 @@ __device__ __forceinline__ void push_body(const DevState& st) {
       uint32_t* dbuf = st.dead_buf + off + 4 * wq0;
       int dead_run = 0;
 
-      // chunk ch of this warp = quads [wq0 + 32 ch, +32); bulk copies run two
-      // chunks ahead of the compute
-      const int nchunks = (int)((wq1 - wq0 + 31) >> 5);
+      // chunk ch of this warp = quads [wq0 + kChunkQuads ch, +kChunkQuads), two
+      // per lane; bulk copies run two chunks ahead of the compute
+      const int nchunks = (wq1 - wq0 + kChunkQuads - 1) / kChunkQuads;
       if (!kDepositOnly && lane == 0 && a != q0) {   // the first sub-range's are issued
         if (nchunks > 0) issue_chunk(st, wstage, wbar, off, wq0, wq1, 0);
         if (nchunks > 1) issue_chunk(st, wstage, wbar, off, wq0, wq1, 1);
       }
       int ch = 0;
-      for (int base = wq0; base < wq1; base += 32, ++ch) {
-        const int q = base + lane;
-        unsigned dm = 0, cm = 0, am = 0;
-        float zz[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        float4 z4s = make_float4(0.f, 0.f, 0.f, 0.f), v4s = z4s;
-        uint4 id4s = make_uint4(0u, 0u, 0u, 0u);
-        if (!kDepositOnly) {
+      bool stop = false;
+      if (!kDepositOnly) {
+        // the warp's leading chunks that hold only live particles: each
+        // lane reads its two quads, the stage is refilled with chunk ch + 2,
+        // then straight-line push and (unless one of the warp's particles
+        // left the gap or the state is sorted) deposit
+        const int live_end = min(wq1, N >> 2);
+        const int nfull = live_end > wq0 ? (live_end - wq0) / kChunkQuads : 0;
+        for (; ch < nfull; ++ch) {
           const int s = ch & 1;
-          const bool arrived = mbar_wait_bounded(&wbar[s], (phase >> s) & 1u, st.wait_limit);
-          if (!__all_sync(0xffffffffu, arrived)) {
-            // the copy did not complete in time: flag it, let this warp's copies
-            // in flight (this stage and the next) land with the full limit, keep
-            // the stage parities in step, and stop this warp's part of the segment
-            if (lane == 0) atomicOr(&st.dyn[inst].err, ERR_TIMEOUT);
-            if (mbar_wait_bounded(&wbar[s], (phase >> s) & 1u)) phase ^= 1u << s;
-            if (ch + 1 < nchunks && mbar_wait_bounded(&wbar[s ^ 1], (phase >> (s ^ 1)) & 1u))
-              phase ^= 1u << (s ^ 1);
+          if (!stage_ready(st, wbar, phase, s, ch, nchunks, inst, lane)) {
+            stop = true;
             break;
           }
-          phase ^= 1u << s;
           const unsigned char* b = wstage + s * kStageBytes;
-          if (q < wq1) {
-            z4s = reinterpret_cast<const float4*>(b)[lane];
-            v4s = reinterpret_cast<const float4*>(b + 512)[lane];
-            id4s = reinterpret_cast<const uint4*>(b + 1024)[lane];
+          float4 zA[2], vA[2];
+          uint4 iA[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int o = 512 * h + 16 * lane;
+            zA[h] = *reinterpret_cast<const float4*>(b + o);
+            vA[h] = *reinterpret_cast<const float4*>(b + kArrBytes + o);
+            iA[h] = *reinterpret_cast<const uint4*>(b + 2 * kArrBytes + o);
           }
           __syncwarp();
           if (lane == 0 && ch + 2 < nchunks) issue_chunk(st, wstage, wbar, off, wq0, wq1, ch + 2);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float4 z4 = zA[h], v4 = vA[h];
+            unsigned dm, cm;
+            push_quad(c, Es2, z4, v4, iA[h], dm, cm);
+            const int q = wq0 + kChunkQuads * ch + 32 * h + lane;
+            __stcs(reinterpret_cast<float4*>(zp + 4 * q), z4);
+            __stcs(reinterpret_cast<float4*>(vzp + 4 * q), v4);
+            if (!agg && !__any_sync(0xffffffffu, dm != 0u)) {
+              deposit_quad(hist, z4, inv_dz, Nz);
+            } else {
+              const float zz[4] = {z4.x, z4.y, z4.z, z4.w};
+              deposit_warp(hist, zz, ~dm & 0xFu, inv_dz, Nz, agg);
+            }
+            if (__any_sync(0xffffffffu, (cm | dm) != 0u))
+              record_events(st, g, inst, q, cm, dm, dbuf, dead_run, lane);
+          }
         }
-        if (base + 32 <= wq1 && 4 * (base + 32) <= N) {
-          // every lane holds four live particles (warp-uniform): straight-line
-          // push and, unless one of the warp's particles left the gap or the
-          // state is sorted, straight-line deposit
-          const int i = 4 * q;
-          float4 z4 = kDepositOnly ? __ldcs(reinterpret_cast<const float4*>(zp + i)) : z4s;
-          if (!kDepositOnly) {
-            float4 v4 = v4s;
-            push_quad(c, Es2, z4, v4, id4s, dm, cm);
-            __stcs(reinterpret_cast<float4*>(zp + i), z4);
-            __stcs(reinterpret_cast<float4*>(vzp + i), v4);
-          }
-          if (!agg && !__any_sync(0xffffffffu, dm != 0u)) {
-            deposit_quad(hist, z4, inv_dz, Nz);
-          } else {
-            zz[0] = z4.x; zz[1] = z4.y; zz[2] = z4.z; zz[3] = z4.w;
-            deposit_warp(hist, zz, ~dm & 0xFu, inv_dz, Nz, agg);
-          }
-        } else {
+      }
+      // the rest: a chunk that ends the warp's range or holds the segment's
+      // last (partial) quad, one particle at a time; k_deposit takes all of
+      // its chunks here
+      for (; !stop && ch < nchunks; ++ch) {
+        const unsigned char* b = nullptr;
+        if (!kDepositOnly) {
+          const int s = ch & 1;
+          if (!stage_ready(st, wbar, phase, s, ch, nchunks, inst, lane)) break;
+          b = wstage + s * kStageBytes;
+        }
+        for (int h = 0; h < kChunkQuads / 32; ++h) {
+          const int q = wq0 + kChunkQuads * ch + 32 * h + lane;
+          unsigned dm = 0, cm = 0, am = 0;
+          float zz[4] = {0.0f, 0.0f, 0.0f, 0.0f};
           if (q < wq1) {
             const int i = 4 * q;
+            float4 z4s = make_float4(0.f, 0.f, 0.f, 0.f), v4s = z4s;
+            uint4 id4s = make_uint4(0u, 0u, 0u, 0u);
+            if (!kDepositOnly) {
+              const int o = 512 * h + 16 * lane;
+              z4s = *reinterpret_cast<const float4*>(b + o);
+              v4s = *reinterpret_cast<const float4*>(b + kArrBytes + o);
+              id4s = *reinterpret_cast<const uint4*>(b + 2 * kArrBytes + o);
+            }
             const float zq[4] = {z4s.x, z4s.y, z4s.z, z4s.w};
             const float vq[4] = {v4s.x, v4s.y, v4s.z, v4s.w};
             const uint32_t iq[4] = {id4s.x, id4s.y, id4s.z, id4s.w};
@@ -671,42 +748,12 @@ __device__ __forceinline__ void push_body(const DevState& st) {
             }
           }
           deposit_warp(hist, zz, am, inv_dz, Nz, agg);
+          if (!kDepositOnly && __any_sync(0xffffffffu, (cm | dm) != 0u))
+            record_events(st, g, inst, q, cm, dm, dbuf, dead_run, lane);
         }
-        if (kDepositOnly) continue;
-        // collision candidates -> compact list; absorbed slots -> this warp's
-        // ordered list (warp scans, one atomic per warp with candidates); most
-        // iterations have neither
-        if (!__any_sync(0xffffffffu, (cm | dm) != 0u)) continue;
-        const int cc = __popc(cm), dc = __popc(dm);
-        int ci = cc, di = dc;
-  #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int yc = __shfl_up_sync(0xffffffffu, ci, o);
-          const int yd = __shfl_up_sync(0xffffffffu, di, o);
-          if (lane >= o) { ci += yc; di += yd; }
-        }
-        const int ctot = __shfl_sync(0xffffffffu, ci, 31);
-        const int dtot = __shfl_sync(0xffffffffu, di, 31);
-        if (ctot) {
-          unsigned cbase = 0;
-          if (lane == 0) cbase = atomicAdd(st.cand_count, (unsigned)ctot);
-          cbase = __shfl_sync(0xffffffffu, cbase, 0);
-          unsigned w = cbase + (unsigned)(ci - cc);
-          for (int k2 = 0; k2 < 4; ++k2) {
-            if (cm & (1u << k2)) {
-              if (w < (unsigned)st.cand_cap)
-                st.cand_buf[w] = ((unsigned long long)g << 32) | (unsigned long long)(4 * q + k2);
-              else
-                atomicOr(&st.dyn[inst].err, ERR_CAPACITY);
-              ++w;
-            }
-          }
-        }
-        if (dtot) {
-          int w = dead_run + di - dc;
-          for (int k2 = 0; k2 < 4; ++k2)
-            if (dm & (1u << k2)) dbuf[w++] = (uint32_t)(4 * q + k2);
-          dead_run += dtot;
+        if (!kDepositOnly) {
+          __syncwarp();
+          if (lane == 0 && ch + 2 < nchunks) issue_chunk(st, wstage, wbar, off, wq0, wq1, ch + 2);
         }
       }
       // concatenate the warps' ordered lists into one list per block
