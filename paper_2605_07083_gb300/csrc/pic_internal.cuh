@@ -85,11 +85,15 @@ struct InstDyn {
   long long pushed;          // particle-steps since creation
 };
 
-// Hand-off between the per-species blocks of the post kernel and the last
-// of them to arrive, which finishes the diode's step.
+// Hand-off from k_mid to the post kernel: absorbed counts, pre-compaction
+// counts, the boundary tallies of the step, and the step number and first
+// new id as they were when the step began (the post kernel closes the step
+// in one of its blocks while the others still use them).
 struct PostScratch {
-  int D[3], N[3], Nn[3];
-  unsigned arrive;
+  int D[3], N[3];
+  uint32_t base_id;
+  int32_t pad;
+  long long step;
   long long cnt[3][2];
   double ke[3][2];
 };

@@ -14,7 +14,7 @@
 //   k_post    : three blocks per diode, one per species: deterministic
 //               hole-filling compaction, then the species' appends
 //               (thermionic emission; ionisation children by parent id and
-//               ion-loss replenishment); the last of the three closes the
+//               ion-loss replenishment); the ion block also closes the
 //               diode's step.
 //   k_field   : the Poisson/E solve alone (after a full deposit).
 //   k_phi     : phi and E of the current state, on request.
@@ -526,6 +526,9 @@ __device__ __forceinline__ void push_body(const DevState& st) {
   if (!kDepositOnly && blockIdx.x == 0) {
     for (int g = threadIdx.x; g <= st.n_seg; g += blockDim.x) st.part[g] = segS[g];
     if (threadIdx.x == 0) st.part[st.n_seg + 1] = Geff;
+    // the ionisation events of this step are counted from zero (k_mid
+    // appends them, the post kernel reads the count)
+    for (int i = threadIdx.x; i < st.n_inst; i += blockDim.x) st.dyn[i].ev_count = 0;
   }
   if ((int)blockIdx.x >= Geff) return;
   long long lo, hi;
@@ -942,8 +945,7 @@ __device__ void update_push_weights(const DevState& st, int G, float* ws, long l
 //   * the collisions of the null-collision candidates (MCC).
 // k_post, per (diode, species): deterministic hole filling, then the
 // species' appends (thermionic electrons; ionisation children ordered by
-// parent id; replenished pairs); the last of a diode's three blocks closes
-// its step.
+// parent id; replenished pairs); the ion block closes the diode's step.
 
 __device__ __forceinline__ void move_particle(const DevState& st, long long off, long long src,
                                               long long dst) {
@@ -1048,6 +1050,9 @@ __device__ void mid_field(const DevState& st, int inst, unsigned char* smem, lon
   if (tid == 0) {
     sNemit = st.dyn[inst].emit_dep ? 0 : emitted_count(ic, step);
     st.dyn[inst].emit_dep = 0;
+    PostScratch* ps = st.post + inst;
+    ps->step = step;
+    ps->base_id = st.dyn[inst].next_id;
   }
   __syncthreads();
   const int Nemit = sNemit;
@@ -1183,13 +1188,14 @@ __global__ void __launch_bounds__(kPostThreads, 2) k_mid(DevState st) {
 // its appends -- thermionic electrons (species 0), ionisation children
 // sorted by parent id and replenished pairs (species 1 and 2) -- with ids and
 // slots every block derives from counts it can read (events, emission
-// count, ions absorbed).  The last of the three to finish (an arrival
-// counter; nothing waits) closes the diode's step.
+// count, ions absorbed).  The ion block also closes the diode's step (window
+// tallies, next id, step counter) as soon as it has the counts; no block
+// waits for another.
 __global__ void __launch_bounds__(kPostThreads, 1) k_post(DevState st) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int ws32[32];
   __shared__ InstConst ic;
-  __shared__ int sE, sNemit, sLast, sDi;
+  __shared__ int sE, sNemit, sDi;
 
   const int inst = blockIdx.x / 3, sp = blockIdx.x - 3 * inst;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -1205,8 +1211,8 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post(DevState st) {
   }
   InstDyn* dyn = st.dyn + inst;
   PostScratch* ps = st.post + inst;
-  const long long step = dyn->step;
-  const uint32_t base_id = dyn->next_id;
+  const long long step = ps->step;
+  const uint32_t base_id = ps->base_id;
   // every thread reads the counts itself (in the round trip of the constants)
   const int D = ps->D[sp], N = ps->N[sp];
   const int g = inst * 3 + sp;
@@ -1230,6 +1236,33 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post(DevState st) {
   }
   __syncthreads();                 // ic, the counts and the list are read by every thread below
   if (tid == 0) sNemit = emitted_count(ic, step);
+  if (sp == 2 && tid == 0) {
+    // ---- the diode's step closes here, while the blocks work on: window
+    // tallies, ids, step.  Nothing in this kernel reads what this writes
+    // (the step and first id come from PostScratch, the event count is
+    // reset by the next push).
+    const int Nem = sNemit, Ev = sE;
+    const int Pt = ic.replenish ? ps->D[2] : 0;
+    const uint32_t id_end = base_id + 2u * (uint32_t)Ev + (uint32_t)Nem + 2u * (uint32_t)Pt;
+    dyn->next_id = id_end;
+    // ids key the random streams: a diode that has handed out all 2^32 of
+    // them would reuse one, so that is reported as running out of capacity
+    if ((unsigned long long)base_id + 2ull * (unsigned)Ev + (unsigned)Nem + 2ull * (unsigned)Pt >
+        0xFFFFFFFFull)
+      atomicOr(&dyn->err, ERR_CAPACITY);
+    if (step >= ic.window_start) {
+      dyn->win_steps += 1;
+      for (int k = 0; k < 3; ++k)
+        for (int w = 0; w < 2; ++w) {
+          dyn->count[k][w] += ps->cnt[k][w];
+          dyn->ke[k][w] += ps->ke[k][w];
+        }
+      dyn->emitted += Nem;
+      dyn->replenished += Pt;
+    }
+    dyn->pushed += (long long)ps->N[0] + ps->N[1] + ps->N[2];
+    dyn->step = step + 1;
+  }
 
   // ---- hole filling: the dead slots below the new count take the live
   // particles above it, in order
@@ -1319,43 +1352,7 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post(DevState st) {
     newN = min(Nn + E + P, cap);
   }
   if (__syncthreads_or(overflow) && tid == 0) atomicOr(&dyn->err, ERR_CAPACITY);
-
-  // every thread's moves and appends are complete and visible before the
-  // arrival
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) {
-    st.seg_count[g] = newN;
-    __threadfence();
-    sLast = (atomicAdd(&ps->arrive, 1u) == 2u);
-  }
-  __syncthreads();
-  if (!sLast || tid != 0) return;
-
-  // ---- the last species block of this diode: window tallies, ids, step
-  __threadfence();
-  const volatile PostScratch* vp = ps;
-  ps->arrive = 0u;
-  const int Pt = ic.replenish ? vp->D[2] : 0;
-  dyn->next_id = id_repl + 2u * (uint32_t)Pt;
-  // ids key the random streams: a diode that has handed out all 2^32 of
-  // them would reuse one, so that is reported as running out of capacity
-  if ((unsigned long long)base_id + 2ull * (unsigned)E + (unsigned)Nemit + 2ull * (unsigned)Pt >
-      0xFFFFFFFFull)
-    atomicOr(&dyn->err, ERR_CAPACITY);
-  if (step >= ic.window_start) {
-    dyn->win_steps += 1;
-    for (int k = 0; k < 3; ++k)
-      for (int w = 0; w < 2; ++w) {
-        dyn->count[k][w] += vp->cnt[k][w];
-        dyn->ke[k][w] += vp->ke[k][w];
-      }
-    dyn->emitted += Nemit;
-    dyn->replenished += Pt;
-  }
-  dyn->pushed += (long long)vp->N[0] + vp->N[1] + vp->N[2];
-  dyn->ev_count = 0;
-  dyn->step = step + 1;
+  if (tid == 0) st.seg_count[g] = newN;
 }
 
 // ------------------------------------------------------------------ profiles
