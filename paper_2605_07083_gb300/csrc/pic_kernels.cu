@@ -947,15 +947,6 @@ __device__ void update_push_weights(const DevState& st, int G, float* ws, long l
 // species' appends (thermionic electrons; ionisation children ordered by
 // parent id; replenished pairs); the ion block closes the diode's step.
 
-__device__ __forceinline__ void move_particle(const DevState& st, long long off, long long src,
-                                              long long dst) {
-  st.z[off + dst] = st.z[off + src];
-  st.vx[off + dst] = st.vx[off + src];
-  st.vy[off + dst] = st.vy[off + src];
-  st.vz[off + dst] = st.vz[off + src];
-  st.id[off + dst] = st.id[off + src];
-}
-
 __device__ __forceinline__ void put_particle(const DevState& st, long long off, long long slot,
                                              float z, float vx, float vy, float vz, uint32_t id) {
   st.z[off + slot] = z;
@@ -1274,22 +1265,50 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post(DevState st) {
       if ((int)dd[mid] < Nn) lo = mid + 1; else hi = mid;
     }
     const int h = lo;
+    // kPer consecutive tail slots per thread: one search, one block scan and
+    // one gather-then-scatter round trip for up to kPer * nt of them
+    constexpr int kPer = 4;
     int run = 0;
-    for (int base = 0; base < D; base += nt) {
-      const int k = base + tid;
-      int live = 0;
-      const int t = Nn + k;
-      if (k < D) {
-        int a2 = h, b2 = D;
-        while (a2 < b2) {
-          const int mid = (a2 + b2) >> 1;
-          if ((int)dd[mid] < t) a2 = mid + 1; else b2 = mid;
+    for (int base = 0; base < D; base += kPer * nt) {
+      const int k0 = base + kPer * tid;
+      const int t0 = Nn + k0;
+      int a2 = h, b2 = D;                        // first listed slot >= t0
+      while (a2 < b2) {
+        const int mid = (a2 + b2) >> 1;
+        if ((int)dd[mid] < t0) a2 = mid + 1; else b2 = mid;
+      }
+      unsigned lm = 0u;
+      int cnt = 0;
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) {
+        if (k0 + u < D) {
+          if (a2 < D && (int)dd[a2] == t0 + u) {
+            ++a2;                                // absorbed: not moved
+          } else {
+            lm |= 1u << u;
+            ++cnt;
+          }
         }
-        live = !(a2 < D && (int)dd[a2] == t);
       }
       int tot;
-      const int r = block_exclusive_scan<int>(live, &tot, ws32) + run;
-      if (live) move_particle(st, off, t, dd[r]);
+      int r = block_exclusive_scan<int>(cnt, &tot, ws32) + run;
+      float z[kPer], vx[kPer], vy[kPer], vz[kPer];
+      uint32_t id[kPer];
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) {
+        if (lm & (1u << u)) {
+          const long long src = off + t0 + u;
+          z[u] = st.z[src];
+          vx[u] = st.vx[src];
+          vy[u] = st.vy[src];
+          vz[u] = st.vz[src];
+          id[u] = st.id[src];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) {
+        if (lm & (1u << u)) put_particle(st, off, dd[r++], z[u], vx[u], vy[u], vz[u], id[u]);
+      }
       run += tot;
     }
     __syncthreads();                 // shared memory is reused below
