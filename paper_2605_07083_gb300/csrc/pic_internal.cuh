@@ -318,6 +318,7 @@ __device__ __forceinline__ unsigned frac_units(float f) {
 constexpr int kChunkQuads = 64;       // quads of one warp chunk (two per lane)
 constexpr int kArrBytes = kChunkQuads * 16;   // one array of a chunk
 constexpr int kStageBytes = 3 * kArrBytes;    // one warp chunk: (z, v_z, id)
+static_assert(kChunkQuads % 32 == 0 && kChunkQuads <= 128, "whole quads per lane");
 constexpr int kWaitLimit = 1 << 20;   // bounded polls (each suspends up to kSuspendNs)
 constexpr uint32_t kSuspendNs = 1000;
 

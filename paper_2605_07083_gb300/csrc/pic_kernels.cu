@@ -675,10 +675,11 @@ __device__ __forceinline__ void push_body(const DevState& st) {
             break;
           }
           const unsigned char* b = wstage + s * kStageBytes;
-          float4 zA[2], vA[2];
-          uint4 iA[2];
+          constexpr int kSub = kChunkQuads / 32;  // quads per lane
+          float4 zA[kSub], vA[kSub];
+          uint4 iA[kSub];
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
+          for (int h = 0; h < kSub; ++h) {
             const int o = 512 * h + 16 * lane;
             zA[h] = *reinterpret_cast<const float4*>(b + o);
             vA[h] = *reinterpret_cast<const float4*>(b + kArrBytes + o);
@@ -687,7 +688,7 @@ __device__ __forceinline__ void push_body(const DevState& st) {
           __syncwarp();
           if (lane == 0 && ch + 2 < nchunks) issue_chunk(st, wstage, wbar, off, wq0, wq1, ch + 2);
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
+          for (int h = 0; h < kSub; ++h) {
             float4 z4 = zA[h], v4 = vA[h];
             unsigned dm, cm;
             push_quad(c, Es2, z4, v4, iA[h], dm, cm);
