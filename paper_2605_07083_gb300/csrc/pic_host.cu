@@ -309,6 +309,9 @@ int set_launch_shape(pic_handle* h) {
   // after every kSubQuads quads, so its share has no upper bound)
   h->G = h->sm_count * per_sm;
   h->st.G = h->G;
+  // k_mid spreads a diode's field and a segment's absorbed list over kp
+  // blocks each when the diodes are few (their FP64 work then shares no SM)
+  h->st.kp = std::max(1, std::min(kMaxParts, h->sm_count / (4 * h->n_inst)));
   h->st.W = h->push_threads / 32;
   h->mcc_blocks = h->sm_count;
   const size_t need = (size_t)h->n_seg * h->G;
@@ -415,6 +418,10 @@ bool sort_due(const pic_handle* h, int64_t step_after) {
   return h->sort_period > 0 && step_after % h->sort_period == 0;
 }
 
+// k_mid: kp field blocks per diode, kp list blocks per segment, one block
+// for the push weights, then the collision blocks
+int mid_blocks(const pic_handle* h) { return 4 * h->n_inst * h->st.kp + 1 + h->mcc_blocks; }
+
 // the profile sampler after a step (device-side test of the sampling rule)
 void launch_profile(pic_handle* h) {
   if (h->st.prof_period > 0)
@@ -424,7 +431,7 @@ void launch_profile(pic_handle* h) {
 // one time step; the sort, when due, follows the step
 cudaError_t launch_step(pic_handle* h) {
   k_push<<<h->G, h->push_threads, h->push_smem, h->stream>>>(h->st);
-  k_mid<<<4 * h->n_inst + h->mcc_blocks, kPostThreads, h->mid_smem, h->stream>>>(h->st);
+  k_mid<<<mid_blocks(h), kPostThreads, h->mid_smem, h->stream>>>(h->st);
   k_post<<<3 * h->n_inst, kPostThreads, h->post_smem, h->stream>>>(h->st);
   launch_profile(h);
   h->host_step += 1;
@@ -442,7 +449,7 @@ int build_graph(pic_handle* h, int len, cudaGraphExec_t* out) {
   if (e != cudaSuccess) return cuda_fail_at(h, e, "cudaStreamBeginCapture");
   for (int i = 0; i < len; ++i) {
     k_push<<<h->G, h->push_threads, h->push_smem, h->stream>>>(h->st);
-    k_mid<<<4 * h->n_inst + h->mcc_blocks, kPostThreads, h->mid_smem, h->stream>>>(h->st);
+    k_mid<<<mid_blocks(h), kPostThreads, h->mid_smem, h->stream>>>(h->st);
     k_post<<<3 * h->n_inst, kPostThreads, h->post_smem, h->stream>>>(h->st);
     launch_profile(h);
     if (sort_due(h, i + 1)) launch_sort(h);
@@ -837,7 +844,7 @@ int pic_profile_steps(pic_handle* h, int64_t n_steps, pic_profile* out) {
     cudaEventRecord(e[0], h->stream);
     k_push<<<h->G, h->push_threads, h->push_smem, h->stream>>>(h->st);
     cudaEventRecord(e[1], h->stream);
-    k_mid<<<4 * h->n_inst + h->mcc_blocks, kPostThreads, h->mid_smem, h->stream>>>(h->st);
+    k_mid<<<mid_blocks(h), kPostThreads, h->mid_smem, h->stream>>>(h->st);
     cudaEventRecord(e[5], h->stream);
     k_post<<<3 * h->n_inst, kPostThreads, h->post_smem, h->stream>>>(h->st);
     launch_profile(h);

@@ -11,6 +11,7 @@ constexpr int kMaxNz = 4096;          // shared-memory grid limit (nodes = Nz + 
 constexpr int kMaxInstances = 1024;
 constexpr int kEvCap = 2048;          // ionisation events per instance per step
 constexpr int kPostThreads = 512;
+constexpr int kMaxParts = 4;          // k_mid blocks per diode field / per segment list
 constexpr int kHistMaxParticles = (1 << 20) - 256;
 // push-block weights (shares of the particle range): nominal, bounds
 constexpr int kNominalWeight = 1024, kMinWeight = 256, kMaxWeight = 4096;
@@ -94,8 +95,8 @@ struct PostScratch {
   uint32_t base_id;
   int32_t pad;
   long long step;
-  long long cnt[3][2];
-  double ke[3][2];
+  long long cnt[3][kMaxParts][2];    // per species, per k_mid list block, per electrode
+  double ke[3][kMaxParts][2];
 };
 
 struct Event {              // one ionisation: parent id + both children
@@ -146,6 +147,7 @@ struct DevState {
   int* bt;                 // [G] streaming time of each block in the last push, ns
   int* bw_n;               // [1] weight updates since the last reset to equal shares
   int agg;
+  int kp;                  // k_mid blocks per diode for its field, per segment for its lists
 };
 
 // Is the state after step n a profile sample?  (Sec. 3 late-time averages:

@@ -793,9 +793,11 @@ __global__ void k_deposit(DevState st) { push_body<true>(st); }
 // d_{j-1}) / (2 dz) inside, one-sided at the electrodes.  phi_j = j d_0 -
 // kappa sum_{k<j} G_k is written only when phi is non-null: the push needs E
 // alone, and FP64 work is scarce on this part.  rho_s is the block's shared
-// copy of the fixed-point charge; it is overwritten with G.
+// copy of the fixed-point charge; it is overwritten with G.  Only nodes in
+// [jlo, jhi) are written: the integer scans are cheap, so several blocks can
+// each solve the whole system and share the FP64 work of writing E.
 __device__ void field_solve(const InstConst& ic, long long* rho_s, float* E, double* phi,
-                            long long* ws) {
+                            long long* ws, int jlo = 0, int jhi = 1 << 30) {
   const int Nz = ic.Nz;
   const int nt = blockDim.x;
   const int c = (Nz + nt - 1) / nt;            // <= 8 for Nz <= 4096, nt = 512
@@ -827,12 +829,13 @@ __device__ void field_solve(const InstConst& ic, long long* rho_s, float* E, dou
     if (u < c && j < Nz) {
       const long long gj = ex + a[u];
       const long long gsum = (j == 0) ? 0LL : gj + gprev;
-      E[j] = (float)fma(B, (double)gsum, A);
+      if (j >= jlo && j < jhi) E[j] = (float)fma(B, (double)gsum, A);
       gprev = gj;
       a[u] = gj;
     }
   }
-  if (j0 < Nz && j0 + c >= Nz) E[Nz] = (float)fma(2.0 * B, (double)gprev, A);   // G_{Nz-1}
+  if (j0 < Nz && j0 + c >= Nz && Nz >= jlo && Nz < jhi)
+    E[Nz] = (float)fma(2.0 * B, (double)gprev, A);                           // G_{Nz-1}
   if (phi) {
     // phi_j = j d0 - kappa sum_{k<j} G_k: a second scan, for sampled or
     // requested potentials only
@@ -848,9 +851,10 @@ __device__ void field_solve(const InstConst& ic, long long* rho_s, float* E, dou
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int j = j0 + u;
-      if (u < c && j < Nz) phi[j] = fma((double)j, d0, -kap * (double)(hex + hx[u]));
+      if (u < c && j < Nz && j >= jlo && j < jhi)
+        phi[j] = fma((double)j, d0, -kap * (double)(hex + hx[u]));
     }
-    if (threadIdx.x == 0) phi[Nz] = ic.V;
+    if (threadIdx.x == 0 && Nz >= jlo && Nz < jhi) phi[Nz] = ic.V;
   }
   __syncthreads();
 }
@@ -1021,32 +1025,35 @@ __device__ void sort_events(const Event* evb, int E, unsigned long long* evk) {
 }
 
 // Field of the new state of one diode (k_mid).
-__device__ void mid_field(const DevState& st, int inst, unsigned char* smem, long long* ws64) {
+__device__ void mid_field(const DevState& st, int inst, int part, unsigned char* smem,
+                          long long* ws64) {
   __shared__ InstConst ic;
   __shared__ int sNemit;
+  __shared__ long long sStep;
   const int tid = threadIdx.x, nt = blockDim.x;
+  const InstConst* icg = st.ic + inst;
+  const int nn = icg->Nz + 1, off = icg->node_off;
   {
-    const int* src = reinterpret_cast<const int*>(st.ic + inst);
+    const int* src = reinterpret_cast<const int*>(icg);
     int* dst = reinterpret_cast<int*>(&ic);
     for (int w = tid; w < (int)(sizeof(InstConst) / 4); w += nt) dst[w] = src[w];
   }
-  __syncthreads();
-  const long long step = st.dyn[inst].step;
-  const int nn = ic.Nz + 1, off = ic.node_off;
+  // the push's charge (k_post clears rho_acc once every part has read it)
   long long* rho_s = reinterpret_cast<long long*>(smem);            // [nn]
-  int64_t* acc = st.rho_acc + off;
-  for (int j = tid; j < nn; j += nt) {
-    rho_s[j] = acc[j];
-    acc[j] = 0;
-  }
+  const int64_t* acc = st.rho_acc + off;
+  for (int j = tid; j < nn; j += nt) rho_s[j] = acc[j];
   if (tid == 0) {
-    sNemit = st.dyn[inst].emit_dep ? 0 : emitted_count(ic, step);
-    st.dyn[inst].emit_dep = 0;
-    PostScratch* ps = st.post + inst;
-    ps->step = step;
-    ps->base_id = st.dyn[inst].next_id;
+    const long long step = st.dyn[inst].step;
+    sStep = step;
+    sNemit = st.dyn[inst].emit_dep ? 0 : emitted_count(*icg, step);
+    if (part == 0) {
+      PostScratch* ps = st.post + inst;
+      ps->step = step;
+      ps->base_id = st.dyn[inst].next_id;
+    }
   }
   __syncthreads();
+  const long long step = sStep;
   const int Nemit = sNemit;
   if (Nemit > 0) {
     // no push block binned this step's emitted electrons (the diode has no
@@ -1070,38 +1077,45 @@ __device__ void mid_field(const DevState& st, int inst, unsigned char* smem, lon
     for (int j = tid; j < nn; j += nt) rho_s[j] -= hist_node(h, j, ic.Nz);
     __syncthreads();
   }
-  for (int j = tid; j < nn; j += nt) st.rho[off + j] = rho_s[j];
+  if (part == 0)
+    for (int j = tid; j < nn; j += nt) st.rho[off + j] = rho_s[j];
+  const int jlo = (int)((long long)part * nn / st.kp);
+  const int jhi = (int)((long long)(part + 1) * nn / st.kp);
   const bool sample = profile_due(st.prof_period, ic.window_start, step);
-  field_solve(ic, rho_s, st.E + off, sample ? st.phi + off : nullptr, ws64);
+  field_solve(ic, rho_s, st.E + off, sample ? st.phi + off : nullptr, ws64, jlo, jhi);
   if (sample) {
     double* pa = st.phi_sum + off;
     const double* ph = st.phi + off;
-    for (int j = tid; j < nn; j += nt) pa[j] += ph[j];
-    if (tid == 0) st.prof_n[inst] += 1;
+    for (int j = jlo + tid; j < jhi; j += nt) pa[j] += ph[j];
+    if (part == 0 && tid == 0) st.prof_n[inst] += 1;
   }
 }
 
-// Ordered absorbed-slot list of one segment and its boundary tallies (k_mid):
-// the push pieces' lists, concatenated in slot order, into dead_buf + off;
-// count, live count before the step and tallies into the diode's hand-off
-// record.
-__device__ void mid_absorbed(const DevState& st, int g, unsigned char* smem, int* ws32,
-                             long long* wsl, double* wsd) {
+// The ordered list of segment g's absorbed slots (the push blocks' lists
+// concatenated in block order, which is slot order) and its boundary
+// tallies.  kp blocks per segment: each finds the whole block prefix and
+// takes the list entries k = part + kp (tid + nt i), so the FP64 kinetic
+// energies are spread over kp SMs; the post kernel adds the parts' sums in
+// part order.
+__device__ void mid_absorbed(const DevState& st, int g, int part, unsigned char* smem,
+                             int* ws32, long long* wsl, double* wsd) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int inst = g / 3, sp = g - 3 * inst;
+  const int G = st.G, kp = st.kp;
+  long long* blo = reinterpret_cast<long long*>(smem);               // [G + 1]
+  int* bpre = reinterpret_cast<int*>(blo + G + 1);                   // [G + 1]
+  // one round trip: block starts and absorbed counts of every launched
+  // block (only those of blocks with work are used), and the segment's
+  // numbers
+  for (int b = tid; b <= G; b += nt) {
+    blo[b] = st.bstart[b];
+    bpre[b] = b < G ? st.dcount[(long long)g * G + b] : 0;
+  }
   const int Geff = (int)st.part[st.n_seg + 1];
   const long long off = st.seg_off[g];
   const int N = st.seg_count[g];
-  const long long qg = (N + 3) >> 2;
   const long long Sg = st.part[g];
-  long long* blo = reinterpret_cast<long long*>(smem);               // [Geff + 1]
-  int* bpre = reinterpret_cast<int*>(blo + Geff + 1);                // [Geff + 1]
-  // block starts and absorbed counts in one pass (a count is used only where
-  // the block overlaps the segment)
-  for (int b = tid; b <= Geff; b += nt) {
-    blo[b] = st.bstart[b];
-    bpre[b] = b < Geff ? st.dcount[(long long)g * st.G + b] : 0;
-  }
+  const long long qg = (N + 3) >> 2;
   __syncthreads();
   int carry = 0;
   for (int base = 0; base < Geff; base += nt) {
@@ -1125,7 +1139,7 @@ __device__ void mid_absorbed(const DevState& st, int g, unsigned char* smem, int
   const double mw = 0.5 * ic.m_d[sp] * ic.weight;
   long long cnt0 = 0, cnt1 = 0;
   double ke0 = 0.0, ke1 = 0.0;
-  for (int k = tid; k < D; k += nt) {
+  for (int k = part + kp * tid; k < D; k += kp * nt) {
     int blo_i = 0, bhi_i = Geff;
     while (bhi_i - blo_i > 1) {
       const int mid = (blo_i + bhi_i) >> 1;
@@ -1143,12 +1157,14 @@ __device__ void mid_absorbed(const DevState& st, int g, unsigned char* smem, int
   block_reduce4(cnt0, cnt1, ke0, ke1, wsl, wsd);
   if (tid == 0) {
     PostScratch* ps = st.post + inst;
-    ps->D[sp] = D;
-    ps->N[sp] = N;
-    ps->cnt[sp][0] = cnt0;
-    ps->cnt[sp][1] = cnt1;
-    ps->ke[sp][0] = ke0;
-    ps->ke[sp][1] = ke1;
+    if (part == 0) {
+      ps->D[sp] = D;
+      ps->N[sp] = N;
+    }
+    ps->cnt[sp][part][0] = cnt0;
+    ps->cnt[sp][part][1] = cnt1;
+    ps->ke[sp][part][0] = ke0;
+    ps->ke[sp][part][1] = ke1;
   }
 }
 
@@ -1161,17 +1177,18 @@ __global__ void __launch_bounds__(kPostThreads, 2) k_mid(DevState st) {
   __shared__ double wsd[64];
   __shared__ long long ws64[32];
   __shared__ int ws32[32];
-  const int b = blockIdx.x, ni = st.n_inst;
-  if (b < ni) {
-    mid_field(st, b, smem, ws64);
-  } else if (b < 4 * ni) {
-    mid_absorbed(st, b - ni, smem, ws32, wsl, wsd);
-  } else if (b == 4 * ni) {
+  const int b = blockIdx.x, kp = st.kp, nf = st.n_inst * kp;
+  if (b < nf) {
+    mid_field(st, b / kp, b % kp, smem, ws64);
+  } else if (b < 4 * nf) {
+    mid_absorbed(st, (b - nf) / kp, (b - nf) % kp, smem, ws32, wsl, wsd);
+  } else if (b == 4 * nf) {
     update_push_weights(st, (int)st.part[st.n_seg + 1], reinterpret_cast<float*>(wsd), ws64);
   } else {
-    const int m = b - 4 * ni - 1;
-    mcc_candidates(st, (unsigned)m * blockDim.x + threadIdx.x,
-                   (unsigned)(gridDim.x - 4 * ni - 1) * blockDim.x);
+    // candidate k goes to block k mod nb, so the collisions' arithmetic is
+    // spread over every collision block's SM
+    const unsigned m = (unsigned)(b - 4 * nf - 1), nb = (unsigned)(gridDim.x - 4 * nf - 1);
+    mcc_candidates(st, threadIdx.x * nb + m, nb * blockDim.x);
   }
 }
 
@@ -1246,14 +1263,27 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post(DevState st) {
       dyn->win_steps += 1;
       for (int k = 0; k < 3; ++k)
         for (int w = 0; w < 2; ++w) {
-          dyn->count[k][w] += ps->cnt[k][w];
-          dyn->ke[k][w] += ps->ke[k][w];
+          long long c = 0;
+          double e = 0.0;
+          for (int r = 0; r < st.kp; ++r) {       // k_mid's list blocks, in order
+            c += ps->cnt[k][r][w];
+            e += ps->ke[k][r][w];
+          }
+          dyn->count[k][w] += c;
+          dyn->ke[k][w] += e;
         }
       dyn->emitted += Nem;
       dyn->replenished += Pt;
     }
     dyn->pushed += (long long)ps->N[0] + ps->N[1] + ps->N[2];
+    dyn->emit_dep = 0;
     dyn->step = step + 1;
+  }
+  if (sp == 2) {
+    // every k_mid field block has read the push's charge: clear it for the
+    // next push
+    int64_t* acc = st.rho_acc + ic.node_off;
+    for (int j = tid; j <= ic.Nz; j += nt) acc[j] = 0;
   }
 
   // ---- hole filling: the dead slots below the new count take the live
