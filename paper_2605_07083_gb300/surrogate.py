@@ -46,13 +46,19 @@ def targets(diag: dict) -> list:
 
 # ---------------------------------------------------------------- batched PIC
 def run_settings(settings, n_flight=2.0e4, cell_m=1.0e-5, seed0=0, max_instances=512,
-                 transits=5.0):
+                 transits=5.0, n_steps=0, min_steps=0, flight_total=0.0):
     """Run every setting to its late-time window on the GPU, batched: settings
-    of similar run length share one handle.  Returns (diagnostics rows, GPU
+    of similar run length share one handle.  n_flight is one count for all or
+    one per setting; flight_total > 0 instead shares that many electrons in
+    flight evenly over the settings.  Returns (diagnostics rows, GPU
     milliseconds, particle-steps)."""
     import torch
-    params = [W.setting_diode(s, n_flight=n_flight, cell_m=cell_m, seed=seed0 + i,
-                              transits=transits) for i, s in enumerate(settings)]
+    if flight_total > 0:
+        n_flight = flight_total / max(len(settings), 1)
+    fl = np.broadcast_to(np.asarray(n_flight, np.float64), (len(settings),))
+    params = [W.setting_diode(s, n_flight=float(fl[i]), cell_m=cell_m, seed=seed0 + i,
+                              transits=transits, n_steps=n_steps, min_steps=min_steps)
+              for i, s in enumerate(settings)]
     order = sorted(range(len(params)), key=lambda i: params[i]["n_steps"])
     rows = [None] * len(params)
     ms, psteps = 0.0, 0
@@ -76,8 +82,12 @@ def run_settings(settings, n_flight=2.0e4, cell_m=1.0e-5, seed0=0, max_instances
     return rows, ms, psteps
 
 
-def build_dataset(n, seed, **kw):
+def build_dataset(n, seed, flight_range=None, **kw):
+    """n Sobol settings run by batched PIC.  With flight_range = (lo, hi) each
+    diode's electron count in flight is drawn log-uniformly from it."""
     settings = W.sobol_settings(n, seed)
+    if flight_range is not None:
+        kw["n_flight"] = W.flight_counts(n, seed + 7, *flight_range)
     rows, ms, ps = run_settings(settings, seed0=seed * 100003, **kw)
     X = features(settings)
     Y = np.array([targets(r) for r in rows], np.float32)
@@ -307,22 +317,38 @@ def guided_search(model, settings, max_err=0.02, **kw):
     return est, cost
 
 
+# The pipeline at the sizes of the learned-extension workloads: training and
+# held-out diodes at the batched sweep's sizes (2.5 um cells, 5e4-4e6
+# emitted electrons in flight, log-uniform), run for five vacuum transit
+# times but at least the sweep's 10,000 steps, 32 diodes per handle; each
+# search round's batch shares 8e6 electrons in flight over its diodes and
+# runs 20,000 steps.
+STATED = {"data": dict(cell_m=2.5e-6, flight_range=(5.0e4, 4.0e6), min_steps=10000,
+                       max_instances=32),
+          "search": dict(cell_m=2.5e-6, flight_total=8.0e6, n_steps=20000, max_instances=64)}
+
+
 def run(n_train=4096, n_test=512, n_search=256, seed=4, n_flight=2.0e4, search_flight=3.0e4,
-        train_steps=3000):
-    """Whole pipeline: PIC dataset, training, held-out error, both searches."""
+        train_steps=3000, stated=False):
+    """Whole pipeline: PIC dataset, training, held-out error, both searches
+    (at the stated sizes above when ``stated``)."""
     t0 = time.time()
-    _, Xtr, Ytr, c_tr = build_dataset(n_train, seed, n_flight=n_flight)
-    _, Xte, Yte, c_te = build_dataset(n_test, seed + 1, n_flight=n_flight)
+    dkw = dict(STATED["data"]) if stated else {"n_flight": n_flight}
+    skw = dict(STATED["search"]) if stated else {"n_flight": search_flight}
+    _, Xtr, Ytr, c_tr = build_dataset(n_train, seed, **dkw)
+    _, Xte, Yte, c_te = build_dataset(n_test, seed + 1, **dkw)
     model = Surrogate(seed)
     hist = model.fit(Xtr, Ytr, steps=train_steps)
     P = model.predict(Xte)
     err = np.abs(P - Yte)
     searches = W.random_settings(n_search, seed + 2)
-    est_p, cost_p = plain_search(searches, n_flight=search_flight)
-    est_g, cost_g = guided_search(model, searches, n_flight=search_flight)
+    est_p, cost_p = plain_search(searches, **skw)
+    est_g, cost_g = guided_search(model, searches, **skw)
     both = ~np.isnan(est_p) & ~np.isnan(est_g)
     agree = np.abs(est_p[both] - est_g[both])
     return {
+        "sizes": {"data": {k: list(v) if isinstance(v, tuple) else v for k, v in dkw.items()},
+                  "search": skw},
         "dataset": {"train": n_train, "test": n_test, "train_cost": c_tr, "test_cost": c_te},
         "training": {"steps": train_steps, "loss_first": hist[0][1], "loss_last": hist[-1][1]},
         "held_out": {"mae": dict(zip(TARGETS, err.mean(0).tolist())),
@@ -347,4 +373,6 @@ if __name__ == "__main__":
     if "--small" in sys.argv:
         kw = dict(n_train=512, n_test=128, n_search=32, n_flight=5.0e3, search_flight=5.0e3,
                   train_steps=1500)
+    if "--stated-sizes" in sys.argv:
+        kw = dict(stated=True)
     print(json.dumps(run(**kw)))

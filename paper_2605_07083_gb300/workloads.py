@@ -281,6 +281,13 @@ def sobol_settings(n: int, seed: int, keys=SURROGATE_KEYS, fixed=None):
     return out
 
 
+def flight_counts(n: int, seed: int, lo: float = 5.0e4, hi: float = 4.0e6) -> np.ndarray:
+    """n emitted-electron counts in flight, log-uniform on [lo, hi] (the
+    uneven per-diode sizes of the batched sweep)."""
+    rng = np.random.default_rng(seed)
+    return 10.0 ** rng.uniform(math.log10(lo), math.log10(hi), n)
+
+
 def random_settings(n: int, seed: int):
     """n uniformly random (T_w, n_gas, gap, bias) settings for the transition
     search (emission flux left free)."""
@@ -296,10 +303,12 @@ def random_settings(n: int, seed: int):
 
 
 def setting_diode(s: dict, n_flight: float = 2.0e4, cell_m: float = 1.0e-5, seed: int = 0,
-                  transits: float = 5.0, window_frac: float = 0.4) -> dict:
+                  transits: float = 5.0, window_frac: float = 0.4, n_steps: int = 0,
+                  min_steps: int = 0) -> dict:
     """He diode of one surrogate setting: cells of ``cell_m``, dt so that an
     electron at the collision-energy bound crosses at most half a cell, a run
-    of ``transits`` vacuum transit times, the last ``window_frac`` averaged;
+    of ``transits`` vacuum transit times (at least ``min_steps``; exactly
+    ``n_steps`` when that is given), the last ``window_frac`` averaged;
     weight for ~n_flight emitted electrons in flight."""
     p = he_defaults()
     gap, V = float(s["gap_m"]), float(s["bias_V"])
@@ -308,12 +317,16 @@ def setting_diode(s: dict, n_flight: float = 2.0e4, cell_m: float = 1.0e-5, seed
     v_cap = math.sqrt(2.0 * E_cap * E_CHARGE / M_E)
     dt = min(1e-12, 0.5 * (gap / Nz) / v_cap)
     t_tr = vacuum_transit_time(gap, V)
-    n_steps = int(math.ceil(transits * t_tr / dt))
+    if n_steps <= 0:
+        n_steps = max(int(min_steps), int(math.ceil(transits * t_tr / dt)))
     p.update(L=gap, V=V, Nz=Nz, dt=dt, n_gas=10.0 ** float(s["log10_n_gas"]),
              T_wall_K=float(s["T_wall_K"]), gamma_emit=float(s["gamma_emit"]),
              E_cap_e_eV=E_cap, E_cap_i_eV=E_cap, seed=seed, n_steps=n_steps,
              window_start=int((1.0 - window_frac) * n_steps))
     p["weight"] = weight_for_in_flight(p["gamma_emit"], gap, V, n_flight)
     x = p["gamma_emit"] * dt / p["weight"]
-    p["capacity"] = (int(3 * n_flight + 2 * x * 64) + 4096, 16384, 16384)
+    # ionisation children grow with the electrons in flight (fewer than one
+    # per electron over these runs)
+    p["capacity"] = (int(3 * n_flight + 2 * x * 64) + 4096, int(2 * n_flight) + 16384,
+                     int(2 * n_flight) + 16384)
     return p
