@@ -64,3 +64,27 @@ def test_window_stationarity_check():
     assert r["stationary"] is False and r["difference"] > r["two_sigma"]
     assert stationarity([0.5, 0.5, 0.5])["stationary"] is None
     assert stationarity([0.4, float("nan"), 0.41, 0.4, 0.42])["blocks"] == 4
+
+
+def test_setting_diode_step_count_rules():
+    """A surrogate setting runs five vacuum transits, at least min_steps, or
+    exactly n_steps; the window is the last 40 % of the run."""
+    s = {"gamma_emit": 7e19, "T_wall_K": 2500.0, "log10_n_gas": 21.5, "gap_m": 3e-3,
+         "bias_V": 10.0}
+    base = W.setting_diode(s, cell_m=2.5e-6)
+    assert base["n_steps"] == math.ceil(5.0 * W.vacuum_transit_time(3e-3, 10.0) / base["dt"])
+    assert W.setting_diode(s, cell_m=2.5e-6, min_steps=10 * base["n_steps"])["n_steps"] == \
+        10 * base["n_steps"]
+    fixed = W.setting_diode(s, cell_m=2.5e-6, n_steps=20000, min_steps=10 ** 9)
+    assert fixed["n_steps"] == 20000 and fixed["window_start"] == 12000
+    # children's capacity grows with the electrons in flight
+    big = W.setting_diode(s, n_flight=4e6)
+    assert big["capacity"][1] >= 8e6 and big["capacity"][2] >= 8e6
+
+
+def test_flight_counts_are_log_uniform_in_range():
+    n = W.flight_counts(20000, 3)
+    assert n.min() >= 5e4 and n.max() <= 4e6
+    u = (np.log10(n) - np.log10(5e4)) / (np.log10(4e6) - np.log10(5e4))
+    assert abs(u.mean() - 0.5) < 0.01 and abs(u.var() - 1 / 12) < 0.003
+    assert np.array_equal(n, W.flight_counts(20000, 3))
