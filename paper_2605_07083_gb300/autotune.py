@@ -65,6 +65,7 @@ def autotune(diode, steps: int = 400, settle: int = 50, threads=THREADS,
                 if s > 0:                      # start the timed steps on a sort
                     step = diode.diagnostics(0)["step"]
                     diode.step((s - step % s) % s)
+                diode.prepare(steps)           # graphs captured outside the timing
                 diode.synchronize()
                 e0.record(diode.stream)
                 diode.step(steps)

@@ -71,8 +71,8 @@ struct pic_handle {
   int sticky = PIC_OK;
   int64_t host_step = 0;        // mirror of the device step counter
   int64_t last_sort_step = 0;
-  // captured step loops, longest first (build_graphs), so that any step
-  // count runs as graphs
+  // step loops by length, longest first (plan_graphs), captured when first
+  // needed, so that any step count runs as graphs
   std::vector<std::pair<int, cudaGraphExec_t>> graphs;
   size_t push_smem = 0, post_smem = 0, field_smem = 0, mid_smem = 0;
   size_t dcount_ints = 0;
@@ -234,7 +234,8 @@ int check_flags(pic_handle* h) {
 }
 
 void drop_graph(pic_handle* h) {
-  for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
+  for (auto& g : h->graphs)
+    if (g.second) cudaGraphExecDestroy(g.second);
   h->graphs.clear();
 }
 
@@ -271,8 +272,9 @@ cudaError_t raise_smem_limits(int device) {
 }
 
 size_t push_smem_bytes(const pic_handle* h, int threads) {
-  return (((size_t)h->max_nodes * 20 + 8 + (size_t)(h->n_seg + 1) * 8 + 127) & ~(size_t)127) +
-         (size_t)(threads / 32) * 2 * (kStageBytes + 8);
+  // Es2 + histogram (20 B per node), segment prefix and offsets, staging
+  const size_t fixed = (size_t)h->max_nodes * 20 + 8 + (size_t)(2 * h->n_seg + 1) * 8;
+  return ((fixed + 127) & ~(size_t)127) + (size_t)(threads / 32) * 2 * (kStageBytes + 8);
 }
 
 // Default threads per push block: the push is issue-bound, and on this part
@@ -478,30 +480,20 @@ int graph_unit(const pic_handle* h) {
   return len <= kMaxGraphSteps ? (int)len : 0;
 }
 
-// All step graphs of the handle at once (the first pic_step after a change
-// of launch shape pays for them): the longest (graph_unit), then u * 2^k for
+// The step graphs' lengths, longest first: graph_unit, then u * 2^k for
 // every u * 2^k below it, u = 1 without a sort and u = sort_period with one.
-// pic_step then runs any step count as graphs, less at most sort_period - 1
-// single steps on each side when a sort is on.
-int build_graphs(pic_handle* h) {
+// pic_step runs any step count as graphs of these lengths, less at most
+// sort_period - 1 single steps on each side when a sort is on.  Each graph
+// is captured the first time a pic_step needs it.
+void plan_graphs(pic_handle* h) {
   drop_graph(h);
   const int top = graph_unit(h);
   const int unit = h->sort_period > 0 ? h->sort_period : 1;
-  std::vector<int> lens{top};
+  h->graphs.push_back({top, nullptr});
   int64_t p = unit;
   while (p * 2 < top) p *= 2;
   for (; p >= unit; p /= 2)
-    if (p < top) lens.push_back((int)p);
-  for (int len : lens) {
-    cudaGraphExec_t g = nullptr;
-    int rc = build_graph(h, len, &g);
-    if (rc != PIC_OK) {
-      drop_graph(h);
-      return rc;
-    }
-    h->graphs.push_back({len, g});
-  }
-  return PIC_OK;
+    if (p < top) h->graphs.push_back({(int)p, nullptr});
 }
 
 void fill_diag(const pic_handle* h, int inst, const InstDyn& d, const int32_t* counts,
@@ -788,43 +780,64 @@ int pic_set_step(pic_handle* h, int64_t step) {
   return PIC_OK;
 }
 
-int pic_step(pic_handle* h, int64_t n_steps) {
-  if (!h || n_steps < 0) return PIC_EINVAL;
-  if (h->sticky != PIC_OK) return h->sticky;
-  int rc = ensure_field(h);
-  if (rc != PIC_OK) return rc;
-  int64_t left = n_steps;
+// The plan of pic_step(n) from the current step: single steps up to a
+// sort-aligned step (with a sort), graphs longest first, single steps for the
+// rest.  With run set it launches the plan; otherwise it only captures the
+// graphs the plan needs (pic_prepare_steps).
+static int step_plan(pic_handle* h, int64_t n_steps, bool run) {
+  int64_t left = n_steps, step = h->host_step;
   const int len = graph_unit(h);
   const int64_t sp = h->sort_period;
   // a graph bakes in where the periodic sort falls, so with a sort the graphs
   // start on sort-aligned steps: single steps up to the next aligned one
   if (len > 0 && sp > 0) {
-    for (; left > 0 && h->host_step % sp != 0; --left) {
+    for (; left > 0 && step % sp != 0; --left, ++step) {
+      if (!run) continue;
       cudaError_t e = launch_step(h);
       if (e != cudaSuccess) return cuda_fail_at(h, e, "step kernel launch");
     }
   }
   if (len > 0 && left > 0) {
-    if (h->graphs.empty() || h->graphs[0].first != len) {
-      rc = build_graphs(h);
-      if (rc != PIC_OK) return rc;
-    }
+    if (h->graphs.empty() || h->graphs[0].first != len) plan_graphs(h);
     // longest first: n steps run as floor(n / len) full graphs and the
     // binary digits of the rest (in sort periods when there is a sort)
-    for (const auto& g : h->graphs) {
+    for (auto& g : h->graphs) {
+      if (left >= g.first && !g.second) {
+        int rc = build_graph(h, g.first, &g.second);
+        if (rc != PIC_OK) return rc;
+      }
       while (left >= g.first) {
-        cudaError_t e = cudaGraphLaunch(g.second, h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e);
-        h->host_step += g.first;
+        if (run) {
+          cudaError_t e = cudaGraphLaunch(g.second, h->stream);
+          if (e != cudaSuccess) return cuda_fail(h, e);
+          h->host_step += g.first;
+        }
         left -= g.first;
+        step += g.first;
       }
     }
   }
-  for (; left > 0; --left) {
+  for (; run && left > 0; --left) {
     cudaError_t e = launch_step(h);
     if (e != cudaSuccess) return cuda_fail_at(h, e, "step kernel launch");
   }
-  return h->sticky;
+  return run ? h->sticky : PIC_OK;
+}
+
+int pic_step(pic_handle* h, int64_t n_steps) {
+  if (!h || n_steps < 0) return PIC_EINVAL;
+  if (h->sticky != PIC_OK) return h->sticky;
+  int rc = ensure_field(h);
+  if (rc != PIC_OK) return rc;
+  return step_plan(h, n_steps, true);
+}
+
+int pic_prepare_steps(pic_handle* h, int64_t n_steps) {
+  if (!h || n_steps < 0) return PIC_EINVAL;
+  if (h->sticky != PIC_OK) return h->sticky;
+  int rc = ensure_field(h);
+  if (rc != PIC_OK) return rc;
+  return step_plan(h, n_steps, false);
 }
 
 int pic_profile_steps(pic_handle* h, int64_t n_steps, pic_profile* out) {

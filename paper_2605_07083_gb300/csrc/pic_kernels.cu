@@ -26,11 +26,15 @@ namespace pic {
 // ------------------------------------------------------------------ partition
 // Every particle kernel splits the concatenation of all (instance, species)
 // segments, in units of 4 particles ("quads"), into G_eff contiguous ranges,
-// one per block.  segS[g] = first quad of segment g, segS[n_seg] = total.
-__device__ void seg_quad_prefix(const DevState& st, long long* segS, long long* ws) {
+// one per block.  segS[g] = first quad of segment g, segS[n_seg] = total;
+// segOff (when given) gets each segment's first slot, loaded in the same
+// round trip.
+__device__ void seg_quad_prefix(const DevState& st, long long* segS, long long* ws,
+                                long long* segOff = nullptr) {
   long long carry = 0;
   for (int base = 0; base < st.n_seg; base += blockDim.x) {
     int g = base + threadIdx.x;
+    if (segOff && g < st.n_seg) segOff[g] = st.seg_off[g];
     long long q = (g < st.n_seg) ? (long long)((st.seg_count[g] + 3) >> 2) : 0LL;
     long long tot;
     long long ex = block_exclusive_scan<long long>(q, &tot, ws);
@@ -506,8 +510,10 @@ __device__ __forceinline__ void push_body(const DevState& st) {
   Hist hist;
   hist.h3 = reinterpret_cast<unsigned*>(smem + (size_t)mn * 8);
   long long* segS = reinterpret_cast<long long*>(smem + (size_t)mn * 20 + ((mn & 1) ? 4 : 0));
+  long long* segOff = segS + st.n_seg + 1;
   // per-warp double-buffered staging of (z, v_z, id) chunks and their mbarriers
-  const size_t stage_off = ((size_t)mn * 20 + 8 + (size_t)(st.n_seg + 1) * 8 + 127) & ~(size_t)127;
+  const size_t stage_off =
+      ((size_t)mn * 20 + 8 + (size_t)(2 * st.n_seg + 1) * 8 + 127) & ~(size_t)127;
   unsigned char* stages = smem + stage_off;
   unsigned long long* bars =
       reinterpret_cast<unsigned long long*>(stages + (size_t)(blockDim.x >> 5) * 2 * kStageBytes);
@@ -520,7 +526,15 @@ __device__ __forceinline__ void push_body(const DevState& st) {
     mbar_init(&bars[2 * (threadIdx.x >> 5) + 1], 1u);
     fence_mbar_init();
   }
-  seg_quad_prefix(st, segS, ws64);
+  // the block's weight prefix is read in the same round trip as the segment
+  // counts and offsets (the total is wG unless fewer blocks get work)
+  long long w0 = 0, w1 = 0, wG = 0;
+  if (!kDepositOnly) {
+    w0 = st.bwp[blockIdx.x];
+    w1 = st.bwp[blockIdx.x + 1];
+    wG = st.bwp[gridDim.x];
+  }
+  seg_quad_prefix(st, segS, ws64, segOff);
   const long long Q = segS[st.n_seg];
   const int Geff = effective_blocks(Q, gridDim.x, blockDim.x);
   if (!kDepositOnly && blockIdx.x == 0) {
@@ -541,10 +555,9 @@ __device__ __forceinline__ void push_body(const DevState& st) {
     // get less and all blocks finish together); the ranges come from exact
     // integer prefix sums of the weights, so they tile [0, Q) exactly.  The
     // prefix is over the launched blocks; blocks past G_eff share nothing.
-    const long long* wp = st.bwp;
-    const long long tot = wp[Geff];
-    lo = Q * wp[blockIdx.x] / tot;
-    hi = Q * wp[blockIdx.x + 1] / tot;
+    const long long tot = Geff == (int)gridDim.x ? wG : st.bwp[Geff];
+    lo = Q * w0 / tot;
+    hi = Q * w1 / tot;
   }
   if (!kDepositOnly && threadIdx.x == 0) {
     // the block ranges, for the post kernel (which would otherwise redo
@@ -581,7 +594,7 @@ __device__ __forceinline__ void push_body(const DevState& st) {
     // and flushed on its own so that no counter of the histogram overflows
     const int q0 = (int)((lo > s0 ? lo : s0) - s0);
     const int q1 = (int)((hi < s1 ? hi : s1) - s0);
-    const long long off = st.seg_off[g];
+    const long long off = segOff[g];
     if (!kDepositOnly && lane == 0) {
       // the warp's first two chunks are in flight while the block stages
       // the diode's constants and field
@@ -1287,8 +1300,12 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post(DevState st) {
   }
 
   // ---- hole filling: the dead slots below the new count take the live
-  // particles above it, in order
+  // particles above it, in order.  The species-0 block draws its first
+  // emitted electrons while the first round's loads are in flight.
   const int Nn = N - D;
+  constexpr int kEmitRegs = 2;
+  float ez[kEmitRegs], evx[kEmitRegs], evy[kEmitRegs], evz[kEmitRegs];
+  bool have_emit = false;
   {
     int lo = 0, hi = D;
     while (lo < hi) {
@@ -1336,6 +1353,14 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post(DevState st) {
           id[u] = st.id[src];
         }
       }
+      if (sp == 0 && base == 0) {
+        const int Ne = sNemit;                   // written before the scan's barriers
+#pragma unroll
+        for (int j = 0; j < kEmitRegs; ++j)
+          if (tid + j * nt < Ne)
+            emitted_electron(ic, tid + j * nt, step, ez[j], evx[j], evy[j], evz[j]);
+        have_emit = true;
+      }
 #pragma unroll
       for (int u = 0; u < kPer; ++u) {
         if (lm & (1u << u)) put_particle(st, off, dd[r++], z[u], vx[u], vy[u], vz[u], id[u]);
@@ -1353,7 +1378,18 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post(DevState st) {
   bool overflow = false;
   int newN = Nn;
   if (sp == 0) {
-    for (int k = tid; k < Nemit; k += nt) {
+    int k = tid;
+#pragma unroll
+    for (int j = 0; j < kEmitRegs; ++j, k += nt) {
+      if (k < Nemit) {
+        float z = ez[j], vx = evx[j], vy = evy[j], vz = evz[j];
+        if (!have_emit) emitted_electron(ic, k, step, z, vx, vy, vz);
+        const long long sl = (long long)Nn + k;
+        if (sl < cap) put_particle(st, off, sl, z, vx, vy, vz, id_emit + (uint32_t)k);
+        else overflow = true;
+      }
+    }
+    for (; k < Nemit; k += nt) {
       float z, vx, vy, vz;
       emitted_electron(ic, k, step, z, vx, vy, vz);
       const long long sl = (long long)Nn + k;

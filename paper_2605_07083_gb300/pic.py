@@ -101,6 +101,7 @@ ENTRY_POINTS = {
                              C.POINTER(_P)]),
     "pic_inject": (C.c_int, [_P, C.c_int, C.c_int, C.c_int64, _P, _P, _P, _P, C.c_int]),
     "pic_step": (C.c_int, [_P, C.c_int64]),
+    "pic_prepare_steps": (C.c_int, [_P, C.c_int64]),
     "pic_profile_steps": (C.c_int, [_P, C.c_int64, C.POINTER(PicProfile)]),
     "pic_diagnostics": (C.c_int, [_P, C.c_int, C.POINTER(PicDiag)]),
     "pic_get_state": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P, _P, _P, C.c_int64,
@@ -250,6 +251,10 @@ def pic_inject(h, instance, species, z, vx, vy, vz):
 
 def pic_step(h, n_steps):
     _check(load().pic_step(h, int(n_steps)), "pic_step", h)
+
+
+def pic_prepare_steps(h, n_steps):
+    _check(load().pic_prepare_steps(h, int(n_steps)), "pic_prepare_steps", h)
 
 
 def pic_profile_steps(h, n_steps) -> dict:
@@ -426,6 +431,10 @@ class Diode:
 
     def step(self, n=1):
         pic_step(self._h, n)
+
+    def prepare(self, n):
+        """Capture now the step graphs that step(n) will launch."""
+        pic_prepare_steps(self._h, n)
 
     def profile(self, n):
         return pic_profile_steps(self._h, n)

@@ -56,6 +56,7 @@ def test_error_strings_and_argument_checks(lib):
     cfg.size = 7                                   # wrong ABI size
     assert lib.pic_create(C.byref(cfg), 1, None, None, C.byref(h)) == pic.PIC_EINVAL
     assert lib.pic_step(None, 1) == pic.PIC_EINVAL
+    assert lib.pic_prepare_steps(None, 1) == pic.PIC_EINVAL
     lib.pic_destroy(None)
 
 

@@ -311,6 +311,37 @@ def test_sort_steps_are_the_same_with_and_without_graphs(env):
     assert np.array_equal(da["count"], db["count"])
 
 
+def test_prepared_graphs_run_the_same_steps(env):
+    """pic_prepare_steps only captures: a handle that prepared 37 steps (and,
+    with a sort period of 5, 12 more from an unaligned step) ends in the same
+    state as one that did not."""
+    pic, O = env
+    p = W.single_diode_small()
+    p["n_gas"] = 2e22
+    state = mixed_state(p, 29, 20000, 8000)
+    runs = []
+    for prep in (False, True):
+        d = pic.Diode(p)
+        for sp in range(3):
+            d.inject(sp, *state[sp])
+        if prep:
+            d.prepare(37)
+        d.step(37)
+        d.tune(sort_period=5, graph_steps=16)
+        d.step(3)
+        if prep:
+            d.prepare(12)
+        d.step(12)
+        runs.append(([d.state(sp) for sp in range(3)], d.rho_fixed(), d.diagnostics()))
+        d.close()
+    (sa, ra, da), (sb, rb, db) = runs
+    assert np.array_equal(ra, rb)
+    for a, b in zip(sa, sb):
+        for k in a:
+            assert np.array_equal(a[k], b[k]), k
+    assert da["step"] == db["step"] == 52
+
+
 def test_autotuner_times_its_grid_and_keeps_the_fastest(env):
     """The autotuner on a reduced grid: one trial per distinct graph length,
     each timed over whole sort periods, and the handle left on the fastest
