@@ -15,7 +15,7 @@ constexpr int kMaxParts = 4;          // k_mid blocks per diode field / per segm
 constexpr int kHistMaxParticles = (1 << 20) - 256;
 // push-block weights (shares of the particle range): nominal, bounds
 constexpr int kNominalWeight = 1024, kMinWeight = 256, kMaxWeight = 4096;
-constexpr int kWeightJumps = 3;    // weight updates that take the measured shares outright
+constexpr int kWeightJumps = 8;    // weight updates that take the measured shares outright
 // quads a push block bins before it flushes its histogram
 constexpr int kSubQuads = kHistMaxParticles / 4;
 constexpr long long kMaxSlots = 1LL << 29;            // particle slots per handle
