@@ -191,8 +191,9 @@ int pic_create(const pic_config* cfgs, int n_instances, void* cuda_stream,
 /* Append n particles of one species to an instance (Sec. 2.1 initial
  * loading).  z in [0, gap_m); velocities in m s^-1, FP32.  Particles get the
  * instance's next ids in order.  Returns PIC_ECAPACITY (nothing appended) if
- * they do not fit, PIC_EINVAL if a host z lies outside [0, L).  Synchronises
- * the stream. */
+ * they do not fit, PIC_EINVAL (nothing appended) if a z lies outside [0, L)
+ * -- checked on the device after the copy, for host and device pointers
+ * alike.  Synchronises the stream. */
 int pic_inject(pic_handle* h, int instance, int species, int64_t n, const float* z,
                const float* vx, const float* vy, const float* vz, int on_device);
 

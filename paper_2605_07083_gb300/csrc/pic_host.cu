@@ -77,6 +77,7 @@ struct pic_handle {
   size_t push_smem = 0, post_smem = 0, field_smem = 0, mid_smem = 0;
   size_t dcount_ints = 0;
   int bstart_len = 0;
+  int* inject_flag = nullptr;   // device word: an injected z outside [0, L)
   int bw_len = 0;
   int mcc_blocks = 0;
   bool sort_ready = false;
@@ -713,10 +714,6 @@ int pic_inject(pic_handle* h, int instance, int species, int64_t n, const float*
   if (!z || !vx || !vy || !vz) return PIC_EINVAL;
   const int g = 3 * instance + species;
   const float Lf = h->ic[instance].L_f;
-  if (!on_device) {
-    for (int64_t i = 0; i < n; ++i)
-      if (!(z[i] >= 0.0f && z[i] < Lf)) return PIC_EINVAL;
-  }
   int32_t count = 0;
   InstDyn d;
   cudaError_t e = cudaMemcpyAsync(&count, h->st.seg_count + g, sizeof(int32_t),
@@ -726,20 +723,13 @@ int pic_inject(pic_handle* h, int instance, int species, int64_t n, const float*
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e);
   if ((int64_t)count + n > h->seg_cap[g]) return PIC_ECAPACITY;
-  if (on_device) {
-    int* bad = (int*)dev_alloc(h, sizeof(int));
-    if (!bad) return PIC_ENOMEM;
-    int hb = 0;
-    e = cudaMemsetAsync(bad, 0, sizeof(int), h->stream);
-    if (e == cudaSuccess) {
-      k_count_outside<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(z, n, Lf, bad);
-      e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e);
-    if (hb) return PIC_EINVAL;
+  if (!h->inject_flag) {
+    h->inject_flag = (int*)dev_alloc(h, sizeof(int));
+    if (!h->inject_flag) return PIC_ENOMEM;
   }
+  // the particles go into the free slots after the live ones and their z
+  // is checked there, on the device; they are counted in only if every z
+  // lies in [0, L), so a rejected call leaves the instance as it was
   const int64_t base = h->seg_off[g] + count;
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const size_t bytes = sizeof(float) * (size_t)n;
@@ -747,13 +737,21 @@ int pic_inject(pic_handle* h, int instance, int species, int64_t n, const float*
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->st.vx + base, vx, bytes, kind, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->st.vy + base, vy, bytes, kind, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->st.vz + base, vz, bytes, kind, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->inject_flag, 0, sizeof(int), h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e);
-  k_fill_ids<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->st.id + base, n, d.next_id);
-  const int32_t newc = (int32_t)(count + n);
-  const uint32_t nid = d.next_id + (uint32_t)n;
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  k_count_outside<<<blocks, 256, 0, h->stream>>>(h->st.z + base, n, Lf, h->inject_flag);
+  k_fill_ids<<<blocks, 256, 0, h->stream>>>(h->st.id + base, n, d.next_id);
+  int hb = 0;
   e = cudaGetLastError();
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(h->st.seg_count + g, &newc, sizeof(int32_t), cudaMemcpyHostToDevice, h->stream);
+    e = cudaMemcpyAsync(&hb, h->inject_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  if (hb) return PIC_EINVAL;
+  const int32_t newc = (int32_t)(count + n);
+  const uint32_t nid = d.next_id + (uint32_t)n;
+  e = cudaMemcpyAsync(h->st.seg_count + g, &newc, sizeof(int32_t), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&h->st.dyn[instance].next_id, &nid, sizeof(uint32_t), cudaMemcpyHostToDevice,
                         h->stream);

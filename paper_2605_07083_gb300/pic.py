@@ -238,9 +238,9 @@ def pic_inject(h, instance, species, z, vx, vy, vz):
     """z, vx, vy, vz: numpy float32 arrays (host) or CUDA float32 tensors."""
     on_dev = hasattr(z, "is_cuda") and z.is_cuda
     if on_dev:
-        ptrs = [t.contiguous().data_ptr() for t in (z, vx, vy, vz)]
-        n = z.numel()
-        keep = None
+        keep = [t.float().contiguous() for t in (z, vx, vy, vz)]   # alive across the call
+        ptrs = [t.data_ptr() for t in keep]
+        n = keep[0].numel()
     else:
         keep = [np.ascontiguousarray(a, dtype=np.float32) for a in (z, vx, vy, vz)]
         ptrs = [a.ctypes.data for a in keep]

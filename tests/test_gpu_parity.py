@@ -201,13 +201,30 @@ def test_capacity_errors_are_reported(env):
 
 
 def test_positions_outside_the_gap_are_rejected(env):
+    """A z outside [0, L) anywhere in a call (host or device arrays, NaN
+    included) rejects the whole call and leaves the instance as it was: the
+    next valid call appends from the same slot and id."""
     pic, O = env
+    import torch
     p = W.single_diode_small()
     d = pic.Diode(p)
     bad = np.array([p["L"] * 1.5], np.float32)
     with pytest.raises(pic.PicError) as e:
         d.inject(0, bad, bad * 0, bad * 0, bad * 0)
     assert e.value.code == pic.PIC_EINVAL
+    z = np.linspace(0.0, p["L"] * 0.99, 1000).astype(np.float32)
+    for k, v in ((0, np.nan), (999, -1e-9), (500, p["L"])):
+        zz = z.copy()
+        zz[k] = v
+        for dev in (False, True):
+            arr = torch.from_numpy(zz).cuda() if dev else zz
+            with pytest.raises(pic.PicError) as e:
+                d.inject(0, arr, arr * 0, arr * 0, arr * 0)
+            assert e.value.code == pic.PIC_EINVAL
+    assert d.state(0)["z"].size == 0
+    d.inject(0, z, z * 0, z * 0, z * 0)
+    st = d.state(0)
+    assert np.array_equal(st["z"], z) and np.array_equal(st["id"], np.arange(1000, dtype=np.uint32))
     d.close()
 
 
