@@ -324,7 +324,12 @@ int set_launch_shape(pic_handle* h) {
     h->st.dcount = (int32_t*)p;
     h->dcount_ints = need;
   }
-  // push-block weights back to equal shares; their times unknown
+  // push-block weights back to their starting shares; their times unknown.
+  // Blocks placed in an earlier round on an SM get more of its issue slots:
+  // measured on the production diode with two blocks per SM, the first
+  // round settles at 1.2x and the second at 0.8x the nominal share, so the
+  // shares start there (and at +-1/3 across three or more rounds, where the
+  // first block ran about twice as fast as the third)
   // layout: bwp [G + 1] long long, bw [G] int, bt [G] int, bw_n [2] int
   const size_t bw_bytes = sizeof(long long) * (size_t)(2 * h->G + 2);
   if (h->G > h->bw_len) {
@@ -338,9 +343,15 @@ int set_launch_shape(pic_handle* h) {
   h->st.bw_n = h->st.bt + h->G;
   {
     std::vector<long long> w((size_t)2 * h->G + 2, 0);
-    for (int b = 0; b <= h->G; ++b) w[b] = (long long)b * kNominalWeight;
     int* wi = reinterpret_cast<int*>(w.data() + h->G + 1);
-    for (int b = 0; b < h->G; ++b) wi[b] = kNominalWeight;
+    const int rounds = std::max(1, h->G / std::max(1, h->sm_count));
+    const double spread = rounds == 2 ? 0.2 : 1.0 / 3.0;
+    for (int b = 0; b < h->G; ++b) {
+      const int k = std::min(b / std::max(1, h->sm_count), rounds - 1);
+      const double f = rounds > 1 ? (rounds - 1 - 2.0 * k) / (rounds - 1) : 0.0;
+      wi[b] = (int)std::lround(kNominalWeight * (1.0 + spread * f));
+      w[b + 1] = w[b] + wi[b];
+    }
     const size_t bytes = bw_bytes;
     cudaError_t e2 = cudaMemcpyAsync(h->st.bwp, w.data(), bytes, cudaMemcpyHostToDevice, h->stream);
     if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(h->stream);
