@@ -396,8 +396,22 @@ __device__ __forceinline__ void push_quad(const SegCtx& c, const float2* Es2, fl
     f2_split(v2, v[k], v[k + 1]);
     f2_split(z2, z[k], z[k + 1]);
   }
+  // wall test of the quad at once: for the bits of z + 0 (the sum turns -0
+  // into +0 and leaves every other value, NaN included, as it is),
+  // 0 <= z < L is an unsigned compare with the bits of L; only a quad with
+  // a particle outside tests each particle
+  {
+    const unsigned long long zero2 = f2_bits(0.0f, 0.0f);
+    float y0, y1, y2, y3;
+    f2_split(add2_rz(f2_bits(z[0], z[1]), zero2), y0, y1);
+    f2_split(add2_rz(f2_bits(z[2], z[3]), zero2), y2, y3);
+    const unsigned hi = max(max(__float_as_uint(y0), __float_as_uint(y1)),
+                            max(__float_as_uint(y2), __float_as_uint(y3)));
+    if (hi >= __float_as_uint(c.Lf)) {
 #pragma unroll
-  for (int k = 0; k < 4; ++k) d |= (z[k] >= 0.0f && z[k] < c.Lf) ? 0u : (1u << k);
+      for (int k = 0; k < 4; ++k) d |= (z[k] >= 0.0f && z[k] < c.Lf) ? 0u : (1u << k);
+    }
+  }
   unsigned m = 0u;
   if (c.tc != 0u) {                      // uniform over the segment
     uint32_t a[4], b[4];
@@ -415,9 +429,12 @@ __device__ __forceinline__ void push_quad(const SegCtx& c, const float2* Es2, fl
         b[k] = (uint32_t)p;
       }
     }
+    // candidates are rare: test the quad's smallest word first
+    if (min(min(a[0], a[1]), min(a[2], a[3])) < c.tc) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) m |= (a[k] < c.tc) ? (1u << k) : 0u;
-    m &= ~d;
+      for (int k = 0; k < 4; ++k) m |= (a[k] < c.tc) ? (1u << k) : 0u;
+      m &= ~d;
+    }
   }
   z4 = make_float4(z[0], z[1], z[2], z[3]);
   v4 = make_float4(v[0], v[1], v[2], v[3]);
