@@ -61,13 +61,15 @@ __device__ __forceinline__ long long warp_start(long long q0, long long q1, int 
 // ------------------------------------------------------------------ deposit
 // Per-block charge histogram in shared memory with native 32-bit atomics.
 // For cell j it keeps three counters side by side (one address, offsets 0,
-// 4, 8): the particle count and the sum of the fixed-point fractions Q = Qh
-// 2^12 + Ql split in two 12-bit halves, so no counter can overflow: a block
-// bins fewer than 2^20 particles (kHistMaxParticles).  Node j's charge is
-// then sign * (cnt_j 2^24 - Qs_j + Qs_{j-1}), Qs = sum Q -- exactly the
-// linear-weight rule, in 64-bit integers at flush time.
+// 4, 8): the particle count n, H = sum (Q >> 12) and L = sum Q mod 2^32 of
+// the fixed-point fractions Q < 2^24.  A block bins fewer than 2^20
+// particles (kHistMaxParticles), so H < 2^32 and the low parts R = sum
+// (Q mod 2^12) < 2^32: sum Q = 2^12 H + R with R = (L - 2^12 H) mod 2^32,
+// exact.  Node j's charge is then sign * (n_j 2^24 - Qs_j + Qs_{j-1}),
+// Qs = sum Q -- exactly the linear-weight rule, in 64-bit integers at flush
+// time.
 struct Hist {
-  unsigned* h3;              // [cell][count, Qh sum, Ql sum]
+  unsigned* h3;              // [cell][count, sum Q >> 12, sum Q mod 2^32]
 };
 
 __device__ __forceinline__ void hist_zero(const Hist& h, int n_cells) {
@@ -75,7 +77,8 @@ __device__ __forceinline__ void hist_zero(const Hist& h, int n_cells) {
 }
 
 __device__ __forceinline__ long long qsum(const Hist& h, int j) {
-  return (long long)h.h3[3 * j + 1] * 4096 + (long long)h.h3[3 * j + 2];
+  const unsigned H = h.h3[3 * j + 1], L = h.h3[3 * j + 2];
+  return (long long)H * 4096 + (long long)(L - (H << 12));
 }
 
 // node charge of cells j-1 and j; callers sync before and after
@@ -97,7 +100,7 @@ __device__ __forceinline__ void hist_add(const Hist& h, int j, unsigned q) {
   unsigned* c = h.h3 + 3 * j;
   atomicAdd(c, 1u);
   atomicAdd(c + 1, q >> 12);
-  atomicAdd(c + 2, q & 4095u);
+  atomicAdd(c + 2, q);
 }
 
 // Deposit up to 4 particles per lane (bit k of am: z[k] is deposited).
@@ -131,7 +134,7 @@ __device__ __forceinline__ void deposit_warp(const Hist& h, const float (&z)[4],
       for (int k = 0; k < 4; ++k) {
         if (am & (1u << k)) {
           const int b = j[k] - wlo;
-          const unsigned qh = q[k] >> 12, ql = q[k] & 4095u;
+          const unsigned qh = q[k] >> 12, ql = q[k];
 #pragma unroll
           for (int t = 0; t < 4; ++t) {
             c[t] += (b == t) ? 1u : 0u;
