@@ -728,14 +728,16 @@ __device__ __forceinline__ void push_body(const DevState& st) {
             const int q = wq0 + kChunkQuads * ch + 32 * h + lane;
             __stcs(reinterpret_cast<float4*>(zp + 4 * q), z4);
             __stcs(reinterpret_cast<float4*>(vzp + 4 * q), v4);
-            if (!agg && !__any_sync(0xffffffffu, dm != 0u)) {
+            // one vote: most quads of a warp have no absorbed particle and
+            // no candidate
+            const bool evt = __any_sync(0xffffffffu, (cm | dm) != 0u);
+            if (!evt && !agg) {
               deposit_quad(hist, z4, inv_dz, Nz);
             } else {
               const float zz[4] = {z4.x, z4.y, z4.z, z4.w};
               deposit_warp(hist, zz, ~dm & 0xFu, inv_dz, Nz, agg);
+              if (evt) record_events(st, g, inst, q, cm, dm, dbuf, dead_run, lane);
             }
-            if (__any_sync(0xffffffffu, (cm | dm) != 0u))
-              record_events(st, g, inst, q, cm, dm, dbuf, dead_run, lane);
           }
         }
       }
