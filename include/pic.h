@@ -133,7 +133,10 @@ typedef struct pic_tuning {
                                  way to exercise the time-out path (the kernel first lets its
                                  copies in flight land, so nothing faults); -2 restores the
                                  default */
-    int32_t reserved[2];
+    int32_t push_chunk;       /* quads each warp of the push streams per chunk, 32 or 64
+                                 (default: 64 unless the cell grid's shared memory then
+                                 leaves fewer resident warps per SM than 32 does) */
+    int32_t reserved[1];
 } pic_tuning;
 
 /* Late-time diagnostics of one instance (Sec. 2.3, Eq. 1-8).  Fluxes in

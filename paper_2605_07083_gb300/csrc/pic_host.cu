@@ -17,6 +17,7 @@
 
 namespace pic {
 __global__ void k_push(DevState st);
+__global__ void k_push32(DevState st);
 __global__ void k_deposit(DevState st);
 __global__ void k_mid(DevState st);
 __global__ void k_post(DevState st);
@@ -65,6 +66,8 @@ struct pic_handle {
   int push_threads = 256, blocks_per_sm = 0, G = 0;   // 0 blocks/SM: occupancy limit
   int sort_period = 0, graph_steps = 64;
   bool threads_set = false;     // push_threads chosen by the caller (pic_tune)
+  int push_chunk = 64;          // quads per warp chunk of the push (64 or 32)
+  bool chunk_set = false;       // push_chunk chosen by the caller (pic_tune)
   DevState st{};
   std::vector<Alloc> allocs;
   bool dirty = true;
@@ -259,7 +262,8 @@ cudaError_t raise_smem_limits(int device) {
   int optin = 0;
   cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   if (e != cudaSuccess) return e;
-  const void* fns[] = {(const void*)k_push, (const void*)k_deposit, (const void*)k_field,
+  const void* fns[] = {(const void*)k_push, (const void*)k_push32,
+                       (const void*)k_deposit, (const void*)k_field,
                        (const void*)k_post, (const void*)k_profile, (const void*)k_phi,
                        (const void*)k_mid};
   for (const void* f : fns) {
@@ -272,39 +276,58 @@ cudaError_t raise_smem_limits(int device) {
   return e;
 }
 
-size_t push_smem_bytes(const pic_handle* h, int threads) {
+size_t push_smem_bytes(const pic_handle* h, int threads, int chunk) {
   // Es2 + histogram (20 B per node), segment prefix and offsets, staging
   const size_t fixed = (size_t)h->max_nodes * 20 + 8 + (size_t)(2 * h->n_seg + 1) * 8;
-  return ((fixed + 127) & ~(size_t)127) + (size_t)(threads / 32) * 2 * (kStageBytes + 8);
+  return ((fixed + 127) & ~(size_t)127) +
+         (size_t)(threads / 32) * 2 * ((size_t)stage_bytes(chunk) + 8);
 }
 
-// Default threads per push block: the push is issue-bound, and on this part
-// about 24 resident warps per SM hide its latencies best (more contend for
-// issue slots, fewer leave dependency waits exposed).  The shared-memory
-// footprint grows with the cell count, so pick the block size that gets
-// closest to 24 warps from below, preferring 384 threads (two blocks per
-// SM) on ties.
-int default_push_threads(const pic_handle* h) {
-  int best = 384, best_w = -1;
-  for (int t : {384, 256, 128, 160, 192, 224, 288, 320, 352}) {
-    int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push, t, push_smem_bytes(h, t)) !=
-        cudaSuccess)
-      continue;
-    const int w = std::min(occ * t / 32, 24);
-    if (w > best_w) { best = t; best_w = w; }
+using PushKernel = void (*)(DevState);
+PushKernel push_kernel(int chunk) { return chunk == 32 ? k_push32 : k_push; }
+
+// resident warps per SM of a push shape (0 if it does not fit)
+int push_warps(const pic_handle* h, int threads, int chunk) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, push_kernel(chunk), threads,
+                                                    push_smem_bytes(h, threads, chunk)) !=
+      cudaSuccess)
+    return 0;
+  return occ * threads / 32;
+}
+
+// Default push shape: the push is issue-bound, and on this part about 24
+// resident warps per SM hide its latencies best (more contend for issue
+// slots, fewer leave dependency waits exposed).  The shared-memory footprint
+// grows with the cell count and the chunk, so pick the block size and chunk
+// that get closest to 24 warps from below, preferring 64-quad chunks, then
+// 384 threads (two blocks per SM), on ties.  A caller's choice of either is
+// kept.
+void default_push_shape(pic_handle* h) {
+  int best_t = h->threads_set ? h->push_threads : 384;
+  int best_c = h->chunk_set ? h->push_chunk : 64;
+  int best_w = -1;
+  for (int c : {64, 32}) {
+    if (h->chunk_set && c != h->push_chunk) continue;
+    for (int t : {384, 256, 128, 160, 192, 224, 288, 320, 352}) {
+      if (h->threads_set && t != h->push_threads) continue;
+      const int w = std::min(push_warps(h, t, c), 24);
+      if (w > best_w) { best_t = t; best_c = c; best_w = w; }
+    }
   }
-  return best;
+  h->push_threads = best_t;
+  h->push_chunk = best_c;
 }
 
 int set_launch_shape(pic_handle* h) {
   cudaError_t e = raise_smem_limits(h->device);
   if (e != cudaSuccess) return cuda_fail(h, e);
-  if (!h->threads_set) h->push_threads = default_push_threads(h);
-  h->push_smem = push_smem_bytes(h, h->push_threads);
+  default_push_shape(h);
+  h->push_smem = push_smem_bytes(h, h->push_threads, h->push_chunk);
   h->field_smem = (size_t)h->max_nodes * 8;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push, h->push_threads, h->push_smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, push_kernel(h->push_chunk),
+                                                    h->push_threads, h->push_smem);
   if (e != cudaSuccess) return cuda_fail(h, e);
   if (occ < 1) occ = 1;
   const int per_sm = h->blocks_per_sm > 0 ? std::min(h->blocks_per_sm, occ) : occ;
@@ -452,7 +475,7 @@ void launch_profile(pic_handle* h) {
 
 // one time step; the sort, when due, follows the step
 cudaError_t launch_step(pic_handle* h) {
-  k_push<<<h->G, h->push_threads, h->push_smem, h->stream>>>(h->st);
+  push_kernel(h->push_chunk)<<<h->G, h->push_threads, h->push_smem, h->stream>>>(h->st);
   k_mid<<<mid_blocks(h), kPostThreads, h->mid_smem, h->stream>>>(h->st);
   k_post<<<3 * h->n_inst, kPostThreads, h->post_smem, h->stream>>>(h->st);
   launch_profile(h);
@@ -470,7 +493,7 @@ int build_graph(pic_handle* h, int len, cudaGraphExec_t* out) {
   cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail_at(h, e, "cudaStreamBeginCapture");
   for (int i = 0; i < len; ++i) {
-    k_push<<<h->G, h->push_threads, h->push_smem, h->stream>>>(h->st);
+    push_kernel(h->push_chunk)<<<h->G, h->push_threads, h->push_smem, h->stream>>>(h->st);
     k_mid<<<mid_blocks(h), kPostThreads, h->mid_smem, h->stream>>>(h->st);
     k_post<<<3 * h->n_inst, kPostThreads, h->post_smem, h->stream>>>(h->st);
     launch_profile(h);
@@ -872,7 +895,7 @@ int pic_profile_steps(pic_handle* h, int64_t n_steps, pic_profile* out) {
   for (int64_t i = 0; i < n_steps; ++i) {
     cudaEvent_t* e = &ev[6 * i];
     cudaEventRecord(e[0], h->stream);
-    k_push<<<h->G, h->push_threads, h->push_smem, h->stream>>>(h->st);
+    push_kernel(h->push_chunk)<<<h->G, h->push_threads, h->push_smem, h->stream>>>(h->st);
     cudaEventRecord(e[1], h->stream);
     k_mid<<<mid_blocks(h), kPostThreads, h->mid_smem, h->stream>>>(h->st);
     cudaEventRecord(e[5], h->stream);
@@ -1270,6 +1293,11 @@ int pic_tune(pic_handle* h, const pic_tuning* t) {
     if (t->push_threads < 64 || t->push_threads > 384 || t->push_threads % 32) return PIC_EINVAL;
     h->push_threads = t->push_threads;
     h->threads_set = true;
+  }
+  if (t->push_chunk != 0) {
+    if (t->push_chunk != 32 && t->push_chunk != 64) return PIC_EINVAL;
+    h->push_chunk = t->push_chunk;
+    h->chunk_set = true;
   }
   if (t->push_blocks_per_sm != 0) {
     if (t->push_blocks_per_sm < 1 || t->push_blocks_per_sm > 32) return PIC_EINVAL;

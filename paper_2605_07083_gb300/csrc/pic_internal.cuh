@@ -317,10 +317,10 @@ __device__ __forceinline__ unsigned frac_units(float f) {
 
 // ---------------------------------------------------------------- bulk copies
 // 1D bulk copies global -> shared completing on an mbarrier (sm_90+ PTX).
-constexpr int kChunkQuads = 64;       // quads of one warp chunk (two per lane)
-constexpr int kArrBytes = kChunkQuads * 16;   // one array of a chunk
-constexpr int kStageBytes = 3 * kArrBytes;    // one warp chunk: (z, v_z, id)
-static_assert(kChunkQuads % 32 == 0 && kChunkQuads <= 128, "whole quads per lane");
+// A warp streams its particles in chunks of cq quads (cq / 32 per lane),
+// double-buffered in shared memory: 64 quads where the cell grid leaves room
+// for ~24 resident warps per SM, 32 where it does not.
+__host__ __device__ constexpr int stage_bytes(int cq) { return 3 * cq * 16; }  // (z, v_z, id)
 constexpr int kWaitLimit = 1 << 20;   // bounded polls (each suspends up to kSuspendNs)
 constexpr uint32_t kSuspendNs = 1000;
 

@@ -448,9 +448,11 @@ __device__ __forceinline__ void push_quad(const SegCtx& c, const float2* Es2, fl
 // Chunk ch of a warp's quads [wq0, wq1) of a segment at slot off: its z,
 // v_z and id into stage ch & 1 of the warp, completing on that stage's
 // mbarrier.  Issued by one lane.
+template <int CQ>
 __device__ __forceinline__ void issue_chunk(const DevState& st, unsigned char* wstage,
                                             unsigned long long* wbar, long long off, int wq0,
                                             int wq1, int ch) {
+  constexpr int kChunkQuads = CQ, kArrBytes = CQ * 16, kStageBytes = stage_bytes(CQ);
   const int s = ch & 1;
   const int qc = wq0 + kChunkQuads * ch;
   const int nq = (wq1 - qc) < kChunkQuads ? (wq1 - qc) : kChunkQuads;
@@ -522,8 +524,10 @@ __device__ __forceinline__ void record_events(const DevState& st, int g, int ins
   }
 }
 
-template <bool kDepositOnly>
+template <bool kDepositOnly, int CQ>
 __device__ __forceinline__ void push_body(const DevState& st) {
+  constexpr int kChunkQuads = CQ, kArrBytes = CQ * 16, kStageBytes = stage_bytes(CQ);
+  static_assert(CQ % 32 == 0 && CQ <= 128, "whole quads per lane");
   extern __shared__ __align__(16) unsigned char smem[];
   const int mn = st.max_nodes;
   float2* Es2 = reinterpret_cast<float2*>(smem);
@@ -620,8 +624,8 @@ __device__ __forceinline__ void push_body(const DevState& st) {
       // the diode's constants and field
       const int b0 = (q1 - q0 > kSubQuads) ? q0 + kSubQuads : q1;
       const int pw0 = (int)warp_start(q0, b0, warp, W), pw1 = (int)warp_start(q0, b0, warp + 1, W);
-      if (pw1 > pw0) issue_chunk(st, wstage, wbar, off, pw0, pw1, 0);
-      if (pw1 - pw0 > kChunkQuads) issue_chunk(st, wstage, wbar, off, pw0, pw1, 1);
+      if (pw1 > pw0) issue_chunk<CQ>(st, wstage, wbar, off, pw0, pw1, 0);
+      if (pw1 - pw0 > kChunkQuads) issue_chunk<CQ>(st, wstage, wbar, off, pw0, pw1, 1);
     }
     if (inst != cur) {
       {
@@ -689,8 +693,8 @@ __device__ __forceinline__ void push_body(const DevState& st) {
       // per lane; bulk copies run two chunks ahead of the compute
       const int nchunks = (wq1 - wq0 + kChunkQuads - 1) / kChunkQuads;
       if (!kDepositOnly && lane == 0 && a != q0) {   // the first sub-range's are issued
-        if (nchunks > 0) issue_chunk(st, wstage, wbar, off, wq0, wq1, 0);
-        if (nchunks > 1) issue_chunk(st, wstage, wbar, off, wq0, wq1, 1);
+        if (nchunks > 0) issue_chunk<CQ>(st, wstage, wbar, off, wq0, wq1, 0);
+        if (nchunks > 1) issue_chunk<CQ>(st, wstage, wbar, off, wq0, wq1, 1);
       }
       int ch = 0;
       bool stop = false;
@@ -719,7 +723,7 @@ __device__ __forceinline__ void push_body(const DevState& st) {
             iA[h] = *reinterpret_cast<const uint4*>(b + 2 * kArrBytes + o);
           }
           __syncwarp();
-          if (lane == 0 && ch + 2 < nchunks) issue_chunk(st, wstage, wbar, off, wq0, wq1, ch + 2);
+          if (lane == 0 && ch + 2 < nchunks) issue_chunk<CQ>(st, wstage, wbar, off, wq0, wq1, ch + 2);
 #pragma unroll
           for (int h = 0; h < kSub; ++h) {
             float4 z4 = zA[h], v4 = vA[h];
@@ -792,7 +796,7 @@ __device__ __forceinline__ void push_body(const DevState& st) {
         }
         if (!kDepositOnly) {
           __syncwarp();
-          if (lane == 0 && ch + 2 < nchunks) issue_chunk(st, wstage, wbar, off, wq0, wq1, ch + 2);
+          if (lane == 0 && ch + 2 < nchunks) issue_chunk<CQ>(st, wstage, wbar, off, wq0, wq1, ch + 2);
         }
       }
       // concatenate the warps' ordered lists into one list per block
@@ -817,8 +821,10 @@ __device__ __forceinline__ void push_body(const DevState& st) {
     st.bt[blockIdx.x] = (int)min(global_ns() - t_start, 2000000000ull);
 }
 
-__global__ void __launch_bounds__(384, 2) k_push(DevState st) { push_body<false>(st); }
-__global__ void k_deposit(DevState st) { push_body<true>(st); }
+// the push with 64-quad and with 32-quad warp chunks
+__global__ void __launch_bounds__(384, 2) k_push(DevState st) { push_body<false, 64>(st); }
+__global__ void __launch_bounds__(384, 2) k_push32(DevState st) { push_body<false, 32>(st); }
+__global__ void k_deposit(DevState st) { push_body<true, 64>(st); }
 
 // ------------------------------------------------------------------ field solve
 // Poisson with Dirichlet phi_0 = 0, phi_Nz = V (Sec. 2.1), solved exactly by

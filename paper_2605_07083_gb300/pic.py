@@ -57,7 +57,7 @@ class PicTuning(C.Structure):
     _fields_ = [("size", C.c_uint32), ("push_threads", C.c_int32),
                 ("push_blocks_per_sm", C.c_int32), ("sort_period", C.c_int32),
                 ("graph_steps", C.c_int32), ("wait_polls", C.c_int32),
-                ("reserved", C.c_int32 * 2)]
+                ("push_chunk", C.c_int32), ("reserved", C.c_int32 * 1)]
 
 
 _DIAG_DOUBLES = [
@@ -364,10 +364,11 @@ def pic_load(h, data: bytes):
 
 
 def pic_tune(h, push_threads=0, push_blocks_per_sm=0, sort_period=0, graph_steps=0,
-             wait_polls=0):
+             wait_polls=0, push_chunk=0):
     t = PicTuning()
     t.size = C.sizeof(PicTuning)
     t.push_threads = push_threads
+    t.push_chunk = push_chunk
     t.push_blocks_per_sm = push_blocks_per_sm
     t.sort_period = sort_period
     t.graph_steps = graph_steps

@@ -455,6 +455,31 @@ def test_energy_above_the_null_collision_bound_is_reported(env):
     assert dg["rc"] == pic.PIC_EENERGYCAP and dg["energy_cap_exceeded"] > 100
 
 
+def test_results_do_not_depend_on_the_push_chunk(env):
+    """Streaming 32- or 64-quad warp chunks changes nothing: 20 collisional
+    steps give bit-identical states, charge and tallies."""
+    pic, O = env
+    p = W.single_diode_small()
+    p.update(n_gas=3e22, replenish=1, window_start=0)
+    st = mixed_state(p, 21, 30001, 10001)
+    out = []
+    for chunk in (64, 32):
+        d = pic.Diode(p)
+        for sp in range(3):
+            d.inject(sp, *st[sp])
+        d.tune(push_chunk=chunk)
+        d.step(20)
+        out.append(([d.state(sp) for sp in range(3)], d.rho_fixed(), d.diagnostics()))
+        d.close()
+    (sa, ra, da), (sb, rb, db) = out
+    assert np.array_equal(ra, rb)
+    for x, y in zip(sa, sb):
+        for k in x:
+            assert np.array_equal(x[k], y[k]), k
+    for k in ("count", "ke", "collisions", "candidates"):
+        assert np.array_equal(da[k], db[k]), k
+
+
 @pytest.mark.parametrize("threads", [160, 320, 384])
 def test_results_do_not_depend_on_the_push_block_size(env, threads):
     """The partition of the particles over push blocks changes nothing: the
