@@ -478,6 +478,11 @@ def test_results_do_not_depend_on_the_push_chunk(env):
             assert np.array_equal(x[k], y[k]), k
     for k in ("count", "ke", "collisions", "candidates"):
         assert np.array_equal(da[k], db[k]), k
+    d = pic.Diode(p)
+    with pytest.raises(pic.PicError) as e:
+        d.tune(push_chunk=48)
+    assert e.value.code == pic.PIC_EINVAL
+    d.close()
 
 
 @pytest.mark.parametrize("threads", [160, 320, 384])
