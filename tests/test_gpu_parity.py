@@ -248,6 +248,33 @@ def test_batched_instances_equal_separate_runs(env):
         assert np.array_equal(da["count"], db["count"])
 
 
+def test_many_instances_equal_separate_runs(env):
+    """13 diodes in one handle split k_mid's work over fewer blocks per diode
+    (its field and absorbed lists) than a handle of one: states, charge and
+    wall counts still match bit for bit, the FP64 energy tallies to
+    rounding (their sums are grouped by those blocks)."""
+    pic, O = env
+    ps = W.batched_sweep(n_instances=13, seed=900, n_steps=100)
+    for p in ps:
+        p["weight"] *= 40.0            # keep the test small
+        p["window_start"] = 0
+    both = pic.Diode(ps)
+    both.step(40)
+    for i, p in enumerate(ps):
+        d = pic.Diode(p)
+        d.step(40)
+        assert np.array_equal(both.rho_fixed(i), d.rho_fixed())
+        for sp in range(3):
+            a, b = by_id(both.state(sp, instance=i)), by_id(d.state(sp))
+            for k in a:
+                assert np.array_equal(a[k], b[k]), (i, sp, k)
+        da, db = both.diagnostics(i), d.diagnostics()
+        assert np.array_equal(da["count"], db["count"])
+        np.testing.assert_allclose(da["ke"], db["ke"], rtol=1e-12)
+        d.close()
+    both.close()
+
+
 # ------------------------------------------------------------ sort
 def test_sort_is_a_stable_permutation_by_cell(env):
     pic, O = env
