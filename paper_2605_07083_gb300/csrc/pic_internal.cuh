@@ -179,23 +179,9 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
   return c;
 }
 
-// Same function, rounds not unrolled: for rare paths, to keep register use low.
-static __device__ __noinline__ uint4 philox10_rolled(uint4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll 1
-  for (int r = 0; r < 10; ++r) {
-    unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
-    unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
-    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1,
-                   (uint32_t)p0);
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
-  }
-  return c;
-}
-
 // Philox2x32-10 word 0 (same paper): one 32x32->64 product per round on a
-// 2-word counter.  The per-particle null-collision candidate word.
-// the same with the ten round keys precomputed (key + r * 0x9E3779B9)
+// 2-word counter, the ten round keys (key + r * 0x9E3779B9) precomputed.
+// The per-particle null-collision candidate word.
 __device__ __forceinline__ uint32_t philox2x32_w0_rk(uint32_t c0, uint32_t c1,
                                                      const uint32_t (&rk)[10]) {
 #pragma unroll
@@ -203,17 +189,6 @@ __device__ __forceinline__ uint32_t philox2x32_w0_rk(uint32_t c0, uint32_t c1,
     const unsigned long long p = (unsigned long long)0xD256D193u * c0;
     c0 = (uint32_t)(p >> 32) ^ rk[r] ^ c1;
     c1 = (uint32_t)p;
-  }
-  return c0;
-}
-
-__device__ __forceinline__ uint32_t philox2x32_w0(uint32_t c0, uint32_t c1, uint32_t k) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const unsigned long long p = (unsigned long long)0xD256D193u * c0;
-    c0 = (uint32_t)(p >> 32) ^ k ^ c1;
-    c1 = (uint32_t)p;
-    k += 0x9E3779B9u;
   }
   return c0;
 }
