@@ -14,6 +14,9 @@ Metric: particle-steps/s (sum over steps of live particles pushed / time).
 N > 1 runs under torchrun: every rank advances its own independent replica
 diode (different seed), no data-path collective; value is the sum over ranks.
 The reference arm times the CPU oracle on a bounded sample of the same state.
+Rank 0 also reports, in the same JSON line, the 64-diode batched sweep
+(10,000 steps in one autotuned handle against the same diodes one by one;
+--no-batched skips it) and the small 128-cell diode.
 """
 from __future__ import annotations
 
