@@ -428,8 +428,8 @@ def run_batched(steps=10_000, warmup=200, tune_steps=400):
             "launch": "one CUDA graph per %d steps, 3 kernels per step (push, mid, post) "
                       "over all 64 diodes" % A.graph_length(tuning["graph_steps"],
                                                             tuning["sort_period"]),
-            "tuning": {k: tuning[k] for k in ("push_threads", "sort_period", "graph_steps",
-                                              "ms_per_step")},
+            "tuning": {k: tuning[k] for k in ("push_threads", "push_chunk", "sort_period",
+                                              "graph_steps", "ms_per_step")},
             "autotune": {"trials": len(tuning["trials"]), "timed_steps_per_trial": tune_steps,
                          "seconds": tune_s,
                          "grid": "threads 128..384 step 32 x sort period {0,25,50,100,200} "

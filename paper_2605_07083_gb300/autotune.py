@@ -4,6 +4,7 @@ Runs real simulation steps through pic_step -- the CUDA-graph path a caller
 uses -- for every candidate shape on a grid of
 
   * threads per block of the particle kernels (128 ... 384 in steps of 32),
+  * optionally the push's warp chunk (64 or 32 quads),
   * the period of the counting sort by cell (0 = never),
   * the number of steps captured in one CUDA graph,
 
@@ -20,6 +21,7 @@ from __future__ import annotations
 THREADS = tuple(range(128, 385, 32))
 SORT_PERIODS = (0, 25, 50, 100, 200)
 GRAPH_STEPS = (16, 64, 256)
+CHUNKS = (64,)
 
 
 def graph_length(graph_steps: int, sort_period: int) -> int:
@@ -34,13 +36,14 @@ def apply(diode, tuning: dict):
     """Set a tuning returned by autotune on a (fresh) handle."""
     diode.tune(push_threads=tuning["push_threads"],
                sort_period=tuning["sort_period"] if tuning["sort_period"] else -1,
-               graph_steps=tuning["graph_steps"])
+               graph_steps=tuning["graph_steps"], push_chunk=tuning.get("push_chunk", 0))
 
 
 def autotune(diode, steps: int = 400, settle: int = 50, threads=THREADS,
-             sort_periods=SORT_PERIODS, graph_steps=GRAPH_STEPS) -> dict:
-    """Return {"push_threads", "sort_period", "graph_steps", "ms_per_step",
-    "trials"} for the fastest shape and apply it to ``diode``.
+             sort_periods=SORT_PERIODS, graph_steps=GRAPH_STEPS, chunks=CHUNKS) -> dict:
+    """Return {"push_threads", "push_chunk", "sort_period", "graph_steps",
+    "ms_per_step", "trials"} for the fastest shape and apply it to
+    ``diode``.
 
     ``steps`` must be a multiple of every sort period tried.  Graph lengths
     that a sort period rounds to the same length are tried once."""
@@ -51,7 +54,7 @@ def autotune(diode, steps: int = 400, settle: int = 50, threads=THREADS,
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     trials = []
-    for t in threads:
+    for t, cq in ((t, cq) for cq in chunks for t in threads):
         for s in sort_periods:
             seen = set()
             for g in graph_steps:
@@ -59,7 +62,8 @@ def autotune(diode, steps: int = 400, settle: int = 50, threads=THREADS,
                 if glen in seen:
                     continue
                 seen.add(glen)
-                tuning = {"push_threads": t, "sort_period": s, "graph_steps": g}
+                tuning = {"push_threads": t, "push_chunk": cq, "sort_period": s,
+                          "graph_steps": g}
                 apply(diode, tuning)
                 diode.step(settle)
                 if s > 0:                      # start the timed steps on a sort
