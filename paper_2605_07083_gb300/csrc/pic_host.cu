@@ -383,6 +383,10 @@ int set_launch_shape(pic_handle* h) {
       wi[b] = (int)std::lround(kNominalWeight * (1.0 + spread * f));
       w[b + 1] = w[b] + wi[b];
     }
+    // the prefix in units of 2^-32 of the total, as the weights block writes it
+    const unsigned long long total = (unsigned long long)w[h->G];
+    for (int b = 1; b <= h->G; ++b)
+      w[b] = (long long)(((unsigned long long)w[b] << 32) / total);
     const size_t bytes = bw_bytes;
     cudaError_t e2 = cudaMemcpyAsync(h->st.bwp, w.data(), bytes, cudaMemcpyHostToDevice, h->stream);
     if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(h->stream);

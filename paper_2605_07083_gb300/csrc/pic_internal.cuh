@@ -143,7 +143,7 @@ struct DevState {
   int64_t* prof_n;         // [n_inst] samples taken
   int wait_limit;          // polls of a push-kernel bulk-copy wait before PIC_ETIMEOUT
   int* bw;                 // [G] push-block weights: each block's share of the particles
-  long long* bwp;          // [G + 1] their prefix sums (the block ranges are Q bwp[b] / bwp[G])
+  long long* bwp;          // [G + 1] their prefix sums in units of 2^-32 of the total (bwp[G] = 2^32)
   int* bt;                 // [G] streaming time of each block in the last push, ns
   int* bw_n;               // [1] weight updates since the last reset to equal shares
   int agg;

@@ -45,11 +45,20 @@ __device__ void seg_quad_prefix(const DevState& st, long long* segS, long long* 
   __syncthreads();
 }
 
-// blocks that get work: at least one quad per thread
+// blocks that get work: at least one quad per thread (the division only
+// when fewer than grid * threads quads leave some blocks idle; Q is then
+// below 2^31)
 __device__ __forceinline__ int effective_blocks(long long Q, int grid, int threads) {
-  long long need = (Q + threads - 1) / threads;
-  if (need < 1) need = 1;
-  return (int)(need < grid ? need : grid);
+  if (Q > (long long)(grid - 1) * threads) return grid;
+  const int need = (int)(((unsigned)Q + (unsigned)threads - 1u) / (unsigned)threads);
+  return need < 1 ? 1 : need;
+}
+
+// floor(Q F / 2^32) for F <= 2^32, exactly (128-bit product); monotone in F
+__device__ __forceinline__ long long scale_frac32(long long Q, unsigned long long F) {
+  const unsigned long long q = (unsigned long long)Q;
+  const unsigned long long lo = q * F, hi = __umul64hi(q, F);
+  return (long long)((hi << 32) | (lo >> 32));
 }
 
 // quad range of warp w of a block range [q0, q1): contiguous, in warp order
@@ -445,6 +454,29 @@ __device__ __forceinline__ void push_quad(const SegCtx& c, const float2* Es2, fl
   cm = m;
 }
 
+// The field of one diode into shared memory as (E_j, E_{j+1} - E_j) pairs,
+// j < Nz, with up to kU loads of each kind in flight per thread: a plain
+// loop waits for one L2 round trip per iteration, which at 2048 cells and
+// 384 threads left every push block ~5 us behind its first particle chunk.
+__device__ __forceinline__ void stage_field(float2* Es2, const float* __restrict__ Eg, int Nz,
+                                            int j_begin = 0) {
+  constexpr int kU = 8;
+  for (int base = j_begin; base < Nz; base += kU * (int)blockDim.x) {
+    float e0[kU], e1[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int j = base + u * (int)blockDim.x + (int)threadIdx.x;
+      e0[u] = j < Nz ? __ldg(Eg + j) : 0.0f;
+      e1[u] = j < Nz ? __ldg(Eg + j + 1) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int j = base + u * (int)blockDim.x + (int)threadIdx.x;
+      if (j < Nz) Es2[j] = make_float2(e0[u], e1[u] - e0[u]);
+    }
+  }
+}
+
 // Chunk ch of a warp's quads [wq0, wq1) of a segment at slot off: its z,
 // v_z and id into stage ch & 1 of the warp, completing on that stage's
 // mbarrier.  Issued by one lane.
@@ -550,17 +582,77 @@ __device__ __forceinline__ void push_body(const DevState& st) {
     mbar_init(&bars[2 * (threadIdx.x >> 5) + 1], 1u);
     fence_mbar_init();
   }
+  // A handle of one diode: every block works on instance 0 (node offset 0,
+  // Nz = max_nodes - 1), so its constants and the first kPre * blockDim.x
+  // field pairs are loaded before the partition is known, in the round trip
+  // of the segment counts.
+  constexpr int kPre = 8;
+  const bool pre = !kDepositOnly && st.n_inst == 1;
+  constexpr int kIcWords = (int)(sizeof(InstConst) / 4);
+  int icw = 0;
+  float pe0[kPre], pe1[kPre];
+  if (pre) {
+    if ((int)threadIdx.x < kIcWords) icw = __ldg(reinterpret_cast<const int*>(st.ic) + threadIdx.x);
+    const int nz = st.max_nodes - 1;
+#pragma unroll
+    for (int u = 0; u < kPre; ++u) {
+      const int j = u * (int)blockDim.x + (int)threadIdx.x;
+      pe0[u] = j < nz ? __ldg(st.E + j) : 0.0f;
+      pe1[u] = j < nz ? __ldg(st.E + j + 1) : 0.0f;
+    }
+  }
   // the block's weight prefix is read in the same round trip as the segment
   // counts and offsets (the total is wG unless fewer blocks get work)
-  long long w0 = 0, w1 = 0, wG = 0;
-  if (!kDepositOnly) {
-    w0 = st.bwp[blockIdx.x];
-    w1 = st.bwp[blockIdx.x + 1];
-    wG = st.bwp[gridDim.x];
+  unsigned long long w0 = 0, w1 = 0;
+  if (!kDepositOnly && threadIdx.x == 0) {
+    w0 = (unsigned long long)st.bwp[blockIdx.x];
+    w1 = (unsigned long long)st.bwp[blockIdx.x + 1];
   }
   seg_quad_prefix(st, segS, ws64, segOff);
   const long long Q = segS[st.n_seg];
-  const int Geff = effective_blocks(Q, gridDim.x, blockDim.x);
+  // One thread finds the block's range and the barrier hands it on (64-bit
+  // divisions here, a long software sequence in every thread, held each
+  // block ~1.7 us; the full grid's path below has none).
+  __shared__ long long range_s[2];
+  __shared__ int geff_s;
+  if (threadIdx.x == 0) {
+    const int Geff = effective_blocks(Q, gridDim.x, blockDim.x);
+    long long lo = 0, hi = 0;
+    if ((int)blockIdx.x < Geff) {
+      if (kDepositOnly) {
+        lo = (long long)blockIdx.x * Q / Geff;
+        hi = ((long long)blockIdx.x + 1) * Q / Geff;
+      } else {
+        // the block's share of the quads is its weight (integer, set from
+        // each block's throughput in the last push, so that SMs that stream
+        // slower get less and all blocks finish together).  bwp holds the
+        // weights' prefix sums as fractions of their total in units of
+        // 2^-32 (bwp[0] = 0, bwp[G] = 2^32), and the ranges are exact
+        // integer functions of it, monotone, so they tile [0, Q) exactly.
+        // When fewer than the launched blocks get work (a state of fewer
+        // quads than threads), the first G_eff blocks share it by their
+        // part of the prefix.
+        if (Geff == (int)gridDim.x) {
+          lo = scale_frac32(Q, w0);
+          hi = scale_frac32(Q, w1);
+        } else {
+          const unsigned long long tot = (unsigned long long)st.bwp[Geff];
+          lo = (long long)((unsigned long long)Q * w0 / tot);
+          hi = (long long)((unsigned long long)Q * w1 / tot);
+        }
+        // the block ranges, for the post kernel (which would otherwise
+        // redo G_eff 64-bit divisions on one SM)
+        st.bstart[blockIdx.x] = lo;
+        if ((int)blockIdx.x == Geff - 1) st.bstart[Geff] = hi;
+      }
+    }
+    range_s[0] = lo;
+    range_s[1] = hi;
+    geff_s = Geff;
+  }
+  __syncthreads();
+  const int Geff = geff_s;
+  const long long lo = range_s[0], hi = range_s[1];
   if (!kDepositOnly && blockIdx.x == 0) {
     for (int g = threadIdx.x; g <= st.n_seg; g += blockDim.x) st.part[g] = segS[g];
     if (threadIdx.x == 0) st.part[st.n_seg + 1] = Geff;
@@ -569,29 +661,26 @@ __device__ __forceinline__ void push_body(const DevState& st) {
     for (int i = threadIdx.x; i < st.n_inst; i += blockDim.x) st.dyn[i].ev_count = 0;
   }
   if ((int)blockIdx.x >= Geff) return;
-  long long lo, hi;
-  if (kDepositOnly) {
-    lo = (long long)blockIdx.x * Q / Geff;
-    hi = ((long long)blockIdx.x + 1) * Q / Geff;
-  } else {
-    // the block's share of the quads is its weight (integer, set from each
-    // block's throughput in the last push, so that SMs that stream slower
-    // get less and all blocks finish together); the ranges come from exact
-    // integer prefix sums of the weights, so they tile [0, Q) exactly.  The
-    // prefix is over the launched blocks; blocks past G_eff share nothing.
-    const long long tot = Geff == (int)gridDim.x ? wG : st.bwp[Geff];
-    lo = Q * w0 / tot;
-    hi = Q * w1 / tot;
-  }
-  if (!kDepositOnly && threadIdx.x == 0) {
-    // the block ranges, for the post kernel (which would otherwise redo
-    // G_eff 64-bit divisions on one SM)
-    st.bstart[blockIdx.x] = lo;
-    if ((int)blockIdx.x == Geff - 1) st.bstart[Geff] = hi;
-  }
   if (lo >= hi) {
     if (!kDepositOnly && threadIdx.x == 0) st.bt[blockIdx.x] = 0;
     return;
+  }
+  int cur = -1;
+  if (pre) {
+    // instance 0's constants and field from the registers loaded above; the
+    // barrier at the start of the segment loop publishes them
+    const int nz = st.max_nodes - 1;
+    int* dst = reinterpret_cast<int*>(&icS);
+    if ((int)threadIdx.x < kIcWords) dst[threadIdx.x] = icw;
+    for (int w = threadIdx.x + blockDim.x; w < kIcWords; w += blockDim.x)
+      dst[w] = reinterpret_cast<const int*>(st.ic)[w];
+#pragma unroll
+    for (int u = 0; u < kPre; ++u) {
+      const int j = u * (int)blockDim.x + (int)threadIdx.x;
+      if (j < nz) Es2[j] = make_float2(pe0[u], pe1[u] - pe0[u]);
+    }
+    stage_field(Es2, st.E, nz, kPre * (int)blockDim.x);
+    cur = 0;
   }
   const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -602,7 +691,6 @@ __device__ __forceinline__ void push_body(const DevState& st) {
     if (segS[mid + 1] > lo) ghi = mid; else glo = mid + 1;
   }
 
-  int cur = -1;
   unsigned phase = 0u;                 // parity of this warp's two stage barriers
   unsigned char* wstage = stages + (size_t)warp * 2 * kStageBytes;
   unsigned long long* wbar = bars + 2 * warp;
@@ -628,19 +716,16 @@ __device__ __forceinline__ void push_body(const DevState& st) {
       if (pw1 - pw0 > kChunkQuads) issue_chunk<CQ>(st, wstage, wbar, off, pw0, pw1, 1);
     }
     if (inst != cur) {
-      {
-        const int* src = reinterpret_cast<const int*>(st.ic + inst);
-        int* dst = reinterpret_cast<int*>(&icS);
-        for (int w = threadIdx.x; w < (int)(sizeof(InstConst) / 4); w += blockDim.x) dst[w] = src[w];
-      }
+      // the diode's constants, and its field read with the node offset and
+      // cell count each thread loads itself, so that the field's loads go
+      // out in the round trip after the constants' (hist_zero below reads
+      // icS after the barrier)
+      const InstConst* icg = st.ic + inst;
+      const int* src = reinterpret_cast<const int*>(icg);
+      int* dst = reinterpret_cast<int*>(&icS);
+      for (int w = threadIdx.x; w < kIcWords; w += blockDim.x) dst[w] = src[w];
+      if (!kDepositOnly) stage_field(Es2, st.E + __ldg(&icg->node_off), __ldg(&icg->Nz));
       __syncthreads();
-      if (!kDepositOnly) {
-        const float* Eg = st.E + icS.node_off;
-        for (int j = threadIdx.x; j < icS.Nz; j += blockDim.x) {
-          const float e0 = Eg[j];
-          Es2[j] = make_float2(e0, Eg[j + 1] - e0);
-        }
-      }
       cur = inst;
     }
     int dead_total = 0;                // absorbed slots the block listed for this segment
@@ -972,6 +1057,11 @@ __device__ void update_push_weights(const DevState& st, int G, float* ws, long l
     if (b < st.G) st.bwp[b + 1] = carry + ex + w;
     carry += tot;
   }
+  // the prefix as fractions of the total in units of 2^-32 (the push turns
+  // them into quad ranges with a multiply); each thread rescales the
+  // entries it wrote, and the total is below 2^31 (G * kMaxWeight)
+  for (int b = threadIdx.x; b < st.G; b += blockDim.x)
+    st.bwp[b + 1] = (long long)(((unsigned long long)st.bwp[b + 1] << 32) / (unsigned long long)carry);
   if (threadIdx.x == 0) {
     st.bwp[0] = 0;
     if (n_upd < kWeightJumps) *st.bw_n = n_upd + 1;
