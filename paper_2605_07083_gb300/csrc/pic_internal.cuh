@@ -129,7 +129,7 @@ struct DevState {
   double* phi;             // [total_nodes]
   int32_t* sort_hist;      // counting-sort histograms, per segment [cell][chunk]
   const int64_t* sort_hoff;  // [n_seg] first histogram entry of each segment
-  unsigned long long* cand_buf;  // [cand_cap] null-collision candidates: (segment << 32) | slot
+  unsigned long long* cand_buf;  // [cand_cap] null-collision candidates: (segment << 32) | absolute slot
   unsigned int* cand_count;      // [1]
   int cand_cap;
   const InstConst* ic;

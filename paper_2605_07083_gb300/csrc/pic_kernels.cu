@@ -296,13 +296,19 @@ __device__ __forceinline__ float collide(const InstConst* __restrict__ icg, Inst
 }
 
 // The collisions of the step's null-collision candidates: thread t of a
-// stride-`stride` team takes candidates t, t + stride, ...
+// stride-`stride` team takes candidates t, t + stride, ...  A record is
+// (segment << 32) | absolute slot; the thread's first record is read in the
+// round trip of the count (a record at or past the count is never used, and
+// the buffer holds cand_cap of them), so a candidate's particle is two round
+// trips from the kernel's start.
 __device__ void mcc_candidates(const DevState& st, unsigned t, unsigned stride) {
-  const unsigned n = min(*st.cand_count, (unsigned)st.cand_cap);
+  const unsigned cap = (unsigned)st.cand_cap;
+  const unsigned long long e_first = t < cap ? st.cand_buf[t] : 0ull;
+  const unsigned n = min(*st.cand_count, cap);
   for (unsigned k = t; k < n; k += stride) {
-    const unsigned long long e = st.cand_buf[k];
+    const unsigned long long e = k == t ? e_first : st.cand_buf[k];
     const int g = (int)(e >> 32);
-    const long long slot = st.seg_off[g] + (long long)(e & 0xffffffffu);
+    const long long slot = (long long)(e & 0xffffffffu);
     const int inst = g / 3, sp = g - 3 * inst;
     const long long step = st.dyn[inst].step;
     int code;
@@ -520,8 +526,8 @@ __device__ __forceinline__ bool stage_ready(const DevState& st, unsigned long lo
 // Collision candidates -> the compact global list (one atomic per warp);
 // absorbed slots -> this warp's ordered list (warp scans).  Called by all 32
 // lanes for a chunk in which some lane has either; q is the lane's quad.
-__device__ __forceinline__ void record_events(const DevState& st, int g, int inst, int q,
-                                              unsigned cm, unsigned dm, uint32_t* dbuf,
+__device__ __forceinline__ void record_events(const DevState& st, int g, int inst, long long off,
+                                              int q, unsigned cm, unsigned dm, uint32_t* dbuf,
                                               int& dead_run, int lane) {
   const int cc = __popc(cm), dc = __popc(dm);
   int ci = cc, di = dc;
@@ -541,7 +547,7 @@ __device__ __forceinline__ void record_events(const DevState& st, int g, int ins
     for (int k2 = 0; k2 < 4; ++k2) {
       if (cm & (1u << k2)) {
         if (w < (unsigned)st.cand_cap)
-          st.cand_buf[w] = ((unsigned long long)g << 32) | (unsigned long long)(4 * q + k2);
+          st.cand_buf[w] = ((unsigned long long)g << 32) | (unsigned long long)(off + 4 * q + k2);
         else
           atomicOr(&st.dyn[inst].err, ERR_CAPACITY);
         ++w;
@@ -825,7 +831,7 @@ __device__ __forceinline__ void push_body(const DevState& st) {
             } else {
               const float zz[4] = {z4.x, z4.y, z4.z, z4.w};
               deposit_warp(hist, zz, ~dm & 0xFu, inv_dz, Nz, agg);
-              if (evt) record_events(st, g, inst, q, cm, dm, dbuf, dead_run, lane);
+              if (evt) record_events(st, g, inst, off, q, cm, dm, dbuf, dead_run, lane);
             }
           }
         }
@@ -877,7 +883,7 @@ __device__ __forceinline__ void push_body(const DevState& st) {
           }
           deposit_warp(hist, zz, am, inv_dz, Nz, agg);
           if (!kDepositOnly && __any_sync(0xffffffffu, (cm | dm) != 0u))
-            record_events(st, g, inst, q, cm, dm, dbuf, dead_run, lane);
+            record_events(st, g, inst, off, q, cm, dm, dbuf, dead_run, lane);
         }
         if (!kDepositOnly) {
           __syncwarp();
@@ -944,10 +950,20 @@ __device__ void field_solve(const InstConst& ic, long long* rho_s, float* E, dou
   // before this thread's first; the total of wl is sum_{j < Nz} G_j
   long long ex, Htot;
   block_exclusive_scan_pair(loc, wl, &ex, &Htot, ws);
-  // E_j = -(d_j + d_{j-1}) / (2 dz) = A + B (G_j + G_{j-1}),  A = -d0/dz, B = kappa/(2 dz)
+  // E_j = -(d_j + d_{j-1}) / (2 dz) = A + B (G_j + G_{j-1}),  A = -d0/dz, B = kappa/(2 dz);
+  // one warp evaluates the constants (FP64 units are few per SM)
+  __shared__ double dAB[3];
   const double kap = ic.kappa;
-  const double d0 = (ic.V + kap * (double)Htot) * ic.inv_nz;
-  const double A = -d0 * ic.inv_dz, B = 0.5 * kap * ic.inv_dz;
+  if (threadIdx.x < 32) {
+    const double d0w = (ic.V + kap * (double)Htot) * ic.inv_nz;
+    if (threadIdx.x == 0) {
+      dAB[0] = d0w;
+      dAB[1] = -d0w * ic.inv_dz;
+      dAB[2] = 0.5 * kap * ic.inv_dz;
+    }
+  }
+  __syncthreads();
+  const double d0 = dAB[0], A = dAB[1], B = dAB[2];
   long long gprev = ex;                        // G_{j0 - 1}
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
@@ -1048,20 +1064,31 @@ __device__ void update_push_weights(const DevState& st, int G, float* ws, long l
     st.bw[b] = (int)fminf(fmaxf(rintf(w), (float)kMinWeight), (float)kMaxWeight);
   }
   __syncthreads();
-  long long carry = 0;
+  // The prefix as fractions of the total in units of 2^-32 (the push turns
+  // them into quad ranges with a multiply).  Any map of the prefix that is
+  // monotone, 0 at 0 and 2^32 at the total tiles the quads exactly; a float
+  // scale is one (rounding keeps order), clamped, with the total's entry
+  // set exactly.  With one pass (G <= blockDim.x) the raw prefix stays in a
+  // register; otherwise each thread rescales the entries it wrote.
+  const bool one_pass = st.G <= (int)blockDim.x;
+  long long carry = 0, mine = 0;
   for (int base = 0; base < st.G; base += blockDim.x) {
     const int b = base + threadIdx.x;
     const long long w = b < st.G ? (long long)st.bw[b] : 0LL;
     long long tot;
     const long long ex = block_exclusive_scan<long long>(w, &tot, ws64);
-    if (b < st.G) st.bwp[b + 1] = carry + ex + w;
+    if (b < st.G) {
+      if (one_pass) mine = carry + ex + w;
+      else st.bwp[b + 1] = carry + ex + w;
+    }
     carry += tot;
   }
-  // the prefix as fractions of the total in units of 2^-32 (the push turns
-  // them into quad ranges with a multiply); each thread rescales the
-  // entries it wrote, and the total is below 2^31 (G * kMaxWeight)
-  for (int b = threadIdx.x; b < st.G; b += blockDim.x)
-    st.bwp[b + 1] = (long long)(((unsigned long long)st.bwp[b + 1] << 32) / (unsigned long long)carry);
+  const float scale = 4294967296.0f / (float)carry;
+  for (int b = threadIdx.x; b < st.G; b += blockDim.x) {
+    const long long P = one_pass ? mine : st.bwp[b + 1];
+    const long long F = (long long)((float)P * scale);
+    st.bwp[b + 1] = b + 1 == st.G ? (1LL << 32) : (F < (1LL << 32) ? F : (1LL << 32));
+  }
   if (threadIdx.x == 0) {
     st.bwp[0] = 0;
     if (n_upd < kWeightJumps) *st.bw_n = n_upd + 1;
@@ -1092,7 +1119,10 @@ __device__ __forceinline__ void put_particle(const DevState& st, long long off, 
   st.id[off + slot] = id;
 }
 
-// sum of (c0, c1, e0, e1) over the block, fixed order; valid in thread 0
+// sum of (c0, c1, e0, e1) over the block, fixed order; valid in thread 0.
+// The FP64 adds (slow on this part: a few FP64 lanes per SM) run only in
+// warps that hold a non-zero energy; adding the zeros would give the same
+// sums.
 __device__ __forceinline__ void block_reduce4(long long& c0, long long& c1, double& e0, double& e1,
                                               long long* wsl, double* wsd) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -1100,8 +1130,13 @@ __device__ __forceinline__ void block_reduce4(long long& c0, long long& c1, doub
   for (int o = 16; o > 0; o >>= 1) {
     c0 += __shfl_down_sync(0xffffffffu, c0, o);
     c1 += __shfl_down_sync(0xffffffffu, c1, o);
-    e0 += __shfl_down_sync(0xffffffffu, e0, o);
-    e1 += __shfl_down_sync(0xffffffffu, e1, o);
+  }
+  if (__any_sync(0xffffffffu, e0 != 0.0 || e1 != 0.0)) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      e0 += __shfl_down_sync(0xffffffffu, e0, o);
+      e1 += __shfl_down_sync(0xffffffffu, e1, o);
+    }
   }
   if (lane == 0) {
     wsl[wid] = c0;
@@ -1119,8 +1154,13 @@ __device__ __forceinline__ void block_reduce4(long long& c0, long long& c1, doub
     for (int o = 16; o > 0; o >>= 1) {
       c0 += __shfl_down_sync(0xffffffffu, c0, o);
       c1 += __shfl_down_sync(0xffffffffu, c1, o);
-      e0 += __shfl_down_sync(0xffffffffu, e0, o);
-      e1 += __shfl_down_sync(0xffffffffu, e1, o);
+    }
+    if (__any_sync(0xffffffffu, e0 != 0.0 || e1 != 0.0)) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        e0 += __shfl_down_sync(0xffffffffu, e0, o);
+        e1 += __shfl_down_sync(0xffffffffu, e1, o);
+      }
     }
   }
   __syncthreads();
@@ -1163,16 +1203,33 @@ __device__ void mid_field(const DevState& st, int inst, int part, unsigned char*
   __shared__ long long sStep;
   const int tid = threadIdx.x, nt = blockDim.x;
   const InstConst* icg = st.ic + inst;
-  const int nn = icg->Nz + 1, off = icg->node_off;
+  // a handle of one diode has node offset 0 and max_nodes nodes: its charge
+  // loads need not wait for the constants
+  const bool one = st.n_inst == 1;
+  const int nn = one ? st.max_nodes : icg->Nz + 1, off = one ? 0 : icg->node_off;
   {
     const int* src = reinterpret_cast<const int*>(icg);
     int* dst = reinterpret_cast<int*>(&ic);
     for (int w = tid; w < (int)(sizeof(InstConst) / 4); w += nt) dst[w] = src[w];
   }
-  // the push's charge (k_post clears rho_acc once every part has read it)
+  // the push's charge (k_post clears rho_acc once every part has read it),
+  // up to kU loads per thread in flight
   long long* rho_s = reinterpret_cast<long long*>(smem);            // [nn]
   const int64_t* acc = st.rho_acc + off;
-  for (int j = tid; j < nn; j += nt) rho_s[j] = acc[j];
+  constexpr int kU = 8;
+  for (int base = 0; base < nn; base += kU * nt) {
+    long long v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int j = base + u * nt + tid;
+      v[u] = j < nn ? acc[j] : 0LL;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int j = base + u * nt + tid;
+      if (j < nn) rho_s[j] = v[u];
+    }
+  }
   if (tid == 0) {
     const long long step = st.dyn[inst].step;
     sStep = step;
