@@ -462,8 +462,8 @@ __device__ __forceinline__ void push_quad(const SegCtx& c, const float2* Es2, fl
 
 // The field of one diode into shared memory as (E_j, E_{j+1} - E_j) pairs,
 // j < Nz, with up to kU loads of each kind in flight per thread: a plain
-// loop waits for one L2 round trip per iteration, which at 2048 cells and
-// 384 threads left every push block ~5 us behind its first particle chunk.
+// loop waits for one L2 round trip per iteration (six at 2048 cells and 384
+// threads, ~1 us of every push block's start).
 __device__ __forceinline__ void stage_field(float2* Es2, const float* __restrict__ Eg, int Nz,
                                             int j_begin = 0) {
   constexpr int kU = 8;
